@@ -1,0 +1,403 @@
+"""Benchmark: normal flows per second of the encoder + flow head on one slice.
+
+One step = one veckm_predict over the whole slice (every event is a requested
+flow): clear, scatter, two pooling passes, window counts, gather fused with
+the perceptron.  Inputs are resident in HBM when the timed region starts; the
+accumulators written by every step (2 x 157 MB at 640x480, D=64) exceed the
+129 MB L2, so no explicit flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--mode bf16|fp16|fp32] [--lean]
+
+Prints one JSON line (rank 0).  With --impl reference the same metric is
+measured for the FP64 CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "normal flows/sec on 1 GB300 (chosen vs plain FP32) at stated err vs FP64; p50/p99 ms"
+UNIT = "flows/s"
+DEFAULT_WORKLOAD = "slice-640x480-2M"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "bf16_tflops": float(pk["bf16_tflops"]),
+                "bf16_tflops_sustained": float(pk.get("bf16_tflops_sustained", pk["bf16_tflops"])),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _kernel_traffic(name: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (source hash recorded beside it)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2504_19417_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(src)):
+        if fn.endswith((".cu", ".h")):
+            with open(os.path.join(src, fn), "rb") as f:
+                h.update(f.read())
+    digest = h.hexdigest()[:16]
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 4 and not ln.startswith("#") and f[0] == name and f[1] == workload:
+            return float(f[2]) if f[3] == digest else None
+    return None
+
+
+def source_digest() -> str:
+    src = os.path.join(ROOT, "paper_2504_19417_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(src)):
+        if fn.endswith((".cu", ".h")):
+            with open(os.path.join(src, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(sl, D, nK, touched, touched_K):
+    """Bytes each kernel must move at minimum (one launch), per the model in the
+    design notes: complex FP32 = 8 B per channel, counts 4 B, events 8 B
+    (x, y int16 + t uint32), flows 8 B."""
+    P = sl.width * sl.height
+    pix = 8 * D
+    return {
+        "clear": P * (pix + 4),
+        "scatter": sl.n * 8 + touched * (pix + 4),
+        "pool_rows": 2 * P * pix,
+        "pool_cols": 2 * P * pix,
+        "counts": 4 * P * 4,
+        "gather": nK * 8 + touched_K * (pix + 4) + nK * 8,
+    }
+
+
+def mlp_flops(nK, D, hidden=128):
+    return 2.0 * nK * (2 * D * hidden + 2 * hidden)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, int(os.environ["RANK"]), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on bounded samples of the workload."""
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2504_19417_gb300 import synth
+    sl, D = synth.workload(args.workload)
+    T, X, Y = synth.frequencies(D, 0)
+    w = synth.mlp_weights(D, 128, 3)
+    rng = np.random.default_rng(7)
+    S = args.ref_sample
+    times = []
+    for i in range(args.warmup + args.steps):
+        K = np.sort(rng.choice(sl.n, S, replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        emb, _ = oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D, 10, 10,
+                                      16_000.0, T, X, Y, K=K)
+        oracle.mlp(emb, w.W1, w.b1, w.W2, w.b2)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = S * len(times) / tot
+    cores = oracle.num_threads()
+    sample = (f"{S} requested events per step (random, all {sl.n} slice events scattered), "
+              f"FP64 pooled form of Algorithm 1 + perceptron, OpenMP over requested events")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "D": D, "window": "21x21"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import torch
+    dist, rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_2504_19417_gb300 import synth
+    from paper_2504_19417_gb300 import veckm as vk
+    modes = {"bf16": vk.MLP_BF16, "fp16": vk.MLP_FP16, "fp32": vk.MLP_FP32}
+    mode = modes[args.mode]
+    w_def = dict(synth.WORKLOADS[args.workload])
+    w_def["seed"] = w_def["seed"] + 100 * rank  # each rank its own independent slice
+    D = w_def.pop("D")
+    sl = synth.event_slice(**w_def)
+    T, X, Y = synth.frequencies(D, 0)
+    w = synth.mlp_weights(D, 128, 3)
+    span = int(sl.t.max()) - sl.t_ref
+    p = vk.Params(width=sl.width, height=sl.height, D=D, dx=10, dy=10, dt_us=16_000,
+                  t_span_us=span)
+    enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=mode)
+    x = torch.from_numpy(sl.x).cuda()
+    y = torch.from_numpy(sl.y).cuda()
+    t = torch.from_numpy(sl.t.view(np.int32)).cuda()
+    nK = sl.n
+    flow = torch.empty((nK, 2), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+
+    def timed(nsteps, per_step=True):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        evs[0].record(stream)
+        for i in range(nsteps):
+            step()
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(nsteps)])
+        total_ms = float(evs[0].elapsed_time(evs[-1]))
+        if dist:
+            tt = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        return total_ms, per, wall
+
+    clocks = ClockSampler(local)
+    if not args.lean:
+        clocks.start()
+    enc.set_timing(not args.lean)
+    total_ms, per, wall = timed(args.steps)
+    launches_per_step = enc.last_launch_count()
+    stage_ms, stage_calls = enc.stage_times() if not args.lean else ({}, {})
+    enc.set_timing(False)
+    clk = clocks.stop() if not args.lean else None
+    enc.sync_status()
+    value = ws * nK * args.steps / (total_ms / 1000.0)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "f32+bf16", "fp16": "f32+f16", "fp32": "f32"}[args.mode],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sensor": f"{sl.width}x{sl.height}",
+                   "events_per_slice": sl.n, "flows_per_step": nK, "D": D, "window": "21x21",
+                   "dt_us": 16_000, "mlp": f"{2 * D}->128->2 ReLU", "mlp_precision": args.mode,
+                   "parallelism": f"replicas x{ws}, one slice per GPU",
+                   "l2": "inputs larger than L2 (each step writes 2 x accumulator grid)"},
+        "gpu_launches": int(launches_per_step * args.steps),
+    }
+    if args.lean:
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    out["clocks"] = clk
+    # per-kernel roofline from CUDA events recorded on the launching stream
+    pk = _peaks()
+    key = sl.y.astype(np.int64) * sl.width + sl.x
+    touched = int(np.unique(key).size)
+    ab = algorithmic_bytes(sl, D, nK, touched, touched)
+    kern = {}
+    for name in stage_ms:
+        n = max(1, int(stage_calls[name]))
+        ms = stage_ms[name] / n
+        kern[name] = {"ms": ms, "GB/s": ab[name] / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                      "bytes": ab[name]}
+    kern["gather"]["TFLOP/s"] = mlp_flops(nK, D) / (kern["gather"]["ms"] * 1e-3) / 1e12
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    kd = kern[dom]
+    if dom == "gather" and mode != vk.MLP_FP32 and \
+            kd["TFLOP/s"] / pk["bf16_tflops_sustained"] > kd["GB/s"] / pk["hbm_gbs"]:
+        roof = {"bound": "tensor", "achieved": kd["TFLOP/s"], "peak": pk["bf16_tflops_sustained"],
+                "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": kd["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["peak_source"] = pk["source"]
+    tr = _kernel_traffic(dom, args.workload)
+    roof["traffic"] = tr
+    roof["algorithmic_bytes"] = kd["bytes"]
+    out["roofline"] = roof
+    out["kernels"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                          for kk, vv in v.items()} for k, v in kern.items()}
+    encoder_ms = sum(kern[k]["ms"] for k in kern if k != "gather")
+    out["encoder_roofline"] = {
+        "algorithmic_bytes": int(sum(ab[k] for k in ab if k != "gather")),
+        "ms": encoder_ms,
+        "frac_of_hbm": (sum(ab[k] for k in ab if k != "gather") / (encoder_ms * 1e-3) / 1e9)
+        / pk["hbm_gbs"] if encoder_ms > 0 else None}
+
+    # plain FP32 form on the same slice and GPU
+    if mode != vk.MLP_FP32:
+        enc.set_mlp_mode(vk.MLP_FP32)
+        pms, pper, _ = timed(max(3, args.steps // 2))
+        out["plain_fp32"] = {"value": ws * nK * len(pper) / (pms / 1000.0),
+                             "ms_per_step": pms / len(pper),
+                             "p50_ms": float(np.percentile(pper, 50)),
+                             "p99_ms": float(np.percentile(pper, 99))}
+        enc.set_mlp_mode(mode)
+
+    # end to end through the public host-buffer entry point (pinned memory)
+    hx = torch.from_numpy(sl.x).pin_memory()
+    hy = torch.from_numpy(sl.y).pin_memory()
+    ht = torch.from_numpy(sl.t.view(np.int32)).pin_memory()
+    hflow = torch.empty((nK, 2), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        enc.predict_host(hx, hy, ht, sl.t_ref, out=hflow, stream=stream)
+    ne = max(3, args.steps // 2)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        enc.predict_host(hx, hy, ht, sl.t_ref, out=hflow, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    out["e2e"] = {"value": ws * nK * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sl.n * 8,
+                  "d2h_bytes_per_step": nK * 8, "ms_per_step": 1000 * e2e_s / ne}
+
+    # CPU baseline: the FP64 oracle on a bounded sample, rank 0 at N=1 only;
+    # the same sample gives the per-output error of this run against FP64.
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(7)
+        S = args.cpu_sample
+        K = np.sort(rng.choice(sl.n, S, replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        emb_ref, _ = oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D,
+                                          10, 10, 16_000.0, T, X, Y, K=K)
+        flow_ref = oracle.mlp(emb_ref, w.W1, w.b1, w.W2, w.b2)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {
+            "value": S / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{S} random requested events of the {sl.n}-event slice (all events "
+                      f"scattered), FP64 pooled form + perceptron, {dt:.1f} s"}
+        Kd = torch.from_numpy(K).cuda()
+        emb_g = enc.encode(x, y, t, sl.t_ref, K=Kd).cpu().numpy().astype(np.float64)
+        flow_g = enc.predict(x, y, t, sl.t_ref, K=Kd).cpu().numpy().astype(np.float64)
+        e_err = np.linalg.norm(emb_g - emb_ref, axis=1) / np.linalg.norm(emb_ref, axis=1)
+        nr = np.linalg.norm(flow_ref, axis=1)
+        f_err = np.linalg.norm(flow_g - flow_ref, axis=1) / np.maximum(nr, 0.25 * np.median(nr))
+        f_abs = np.abs(flow_g - flow_ref)
+        out["err_vs_fp64"] = {
+            "sample": S, "emb_rel_l2_max": float(e_err.max()), "emb_rel_l2_mean": float(e_err.mean()),
+            "flow_rel_max": float(f_err.max()), "flow_rel_mean": float(f_err.mean()),
+            "flow_abs_max": float(f_abs.max()), "flow_abs_mean": float(f_abs.mean()),
+            "flow_rel_floor": "0.25 x median |flow|"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--lean", action="store_true", help="timed device loop only (for profilers)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=50_000)
+    ap.add_argument("--ref-sample", type=int, default=20_000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

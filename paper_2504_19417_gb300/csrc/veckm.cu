@@ -1,0 +1,484 @@
+// Host side of the C ABI declared in include/veckm.h: context creation,
+// FP64 phase-table construction, stream-ordered launches, error reporting and
+// per-stage timing.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "veckm_internal.h"
+
+using namespace veckm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+veckm_status fail(veckm_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+veckm_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? VECKM_ENOMEM : VECKM_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): output i is mix(seed + (i+1) * gamma).
+uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+constexpr int kStages = 6;  // clear, scatter, pool rows, pool cols, counts, gather
+
+}  // namespace
+
+struct veckm_ctx {
+  int device = 0;
+  Geometry g{};
+  int hidden = 0;
+  uint32_t flags = 0;
+  int64_t dt_us = 0, t_span = 0;
+  double sigma2 = 25.0;
+  std::vector<double> T, X, Y;
+  // device state
+  float4 *tx = nullptr, *ty = nullptr, *tt_lo = nullptr, *tt_hi = nullptr;
+  int nhi = 0;
+  float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
+  uint16_t *W1h = nullptr;
+  float4 *acc = nullptr, *hbuf = nullptr;
+  int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
+  std::vector<float> hW1;  // host copy (re-encoding on precision switch)
+  // staging for the host-buffer entry point
+  void *st_buf = nullptr;
+  size_t st_cap = 0;
+  int *h_err = nullptr;  // pinned
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::vector<cudaEvent_t>> pending;
+  double stage_ms[kStages] = {};
+  int64_t stage_launch[kStages] = {};
+  int last_launches = 0;
+
+  Tables tables() const { return Tables{tx, ty, tt_lo, tt_hi}; }
+  MLP mlp() const {
+    return MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0};
+  }
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// exp(i n w_d) for n in [0, rows) as interleaved FP32 (re, im), channel fastest.
+// The angle n * w_d is formed in FP64 (|n w| stays below ~1e6 rad, where FP64
+// keeps ~1e-10 rad), then rounded once to FP32 per component.
+std::vector<float> phase_rows(const std::vector<double> &w, double scale, int64_t rows,
+                              int64_t step) {
+  const size_t D = w.size();
+  std::vector<float> out((size_t)rows * D * 2);
+  for (int64_t n = 0; n < rows; ++n)
+    for (size_t d = 0; d < D; ++d) {
+      const double a = (double)(n * step) * (w[d] * scale);
+      out[((size_t)n * D + d) * 2] = (float)std::cos(a);
+      out[((size_t)n * D + d) * 2 + 1] = (float)std::sin(a);
+    }
+  return out;
+}
+
+uint16_t half_bits(float v, bool fp16) {
+  if (fp16) {
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+  }
+  __nv_bfloat16 b = __float2bfloat16_rn(v);
+  return *reinterpret_cast<uint16_t *>(&b);
+}
+
+// W1 [hidden][IN] -> core-matrix order used by the tcgen05 kernel:
+// byte (n/8)*16*IN + (k/8)*128 + (n%8)*16 + (k%8)*2.
+std::vector<uint16_t> w1_core_matrix(const std::vector<float> &W1, int hidden, int IN, bool fp16) {
+  std::vector<uint16_t> out((size_t)hidden * IN);
+  for (int n = 0; n < hidden; ++n)
+    for (int k = 0; k < IN; ++k) {
+      const size_t byte = (size_t)(n / 8) * 16 * IN + (size_t)(k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+      out[byte / 2] = half_bits(W1[(size_t)n * IN + k], fp16);
+    }
+  return out;
+}
+
+void free_all(veckm_ctx *c) {
+  void *ptrs[] = {c->tx, c->ty, c->tt_lo, c->tt_hi, c->W1, c->W1t, c->b1, c->W2, c->b2,
+                  c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  for (auto &v : c->pending)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+}
+
+cudaEvent_t take_event(veckm_ctx *c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const void *t,
+                               int64_t n, const void *K, int64_t nK, const void *out) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  if (n < 0 || nK < 0) return fail(VECKM_EINVAL, "negative size (n=%lld, nK=%lld)", (long long)n, (long long)nK);
+  if (n > 0 && (!x || !y || !t)) return fail(VECKM_EINVAL, "null event buffer with n=%lld", (long long)n);
+  if (!K && nK != n) return fail(VECKM_EINVAL, "K is NULL but nK (%lld) != n (%lld)", (long long)nK, (long long)n);
+  if (nK > 0 && !out) return fail(VECKM_EINVAL, "null output buffer");
+  if (nK > 0 && n == 0) return fail(VECKM_EINVAL, "nK > 0 with an empty slice");
+  if (n >= (int64_t)1 << 31) return fail(VECKM_EINVAL, "n too large (%lld)", (long long)n);
+  return VECKM_OK;
+}
+
+enum class Out { Emb, Flow };
+
+veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_t *t, int64_t n,
+                 uint32_t t_ref, const int64_t *K, int64_t nK, float *out, cudaStream_t s, Out what) {
+  veckm_status st = check_events_args(c, x, y, t, n, K, nK, out);
+  if (st) return st;
+  c->last_launches = 0;
+  if (nK == 0 && n == 0) return VECKM_OK;
+  const Geometry &g = c->g;
+  const Events ev{x, y, t, n, t_ref, (uint32_t)c->t_span};
+  const Tables tb = c->tables();
+  std::vector<cudaEvent_t> evs;
+  auto mark = [&]() {
+    if (c->timing) {
+      cudaEvent_t e = take_event(c);
+      cudaEventRecord(e, s);
+      evs.push_back(e);
+    }
+  };
+  const size_t P = (size_t)g.W * g.H;
+  int launches = 0, r;
+  mark();
+  cudaError_t e = cudaMemsetAsync(c->acc, 0, P * g.U * sizeof(float4), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the accumulators");
+  mark();
+  if ((r = launch_scatter(ev, g, tb, c->acc, c->cnt, c->err, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "scatter launch");
+  launches += r;
+  mark();
+  if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
+  launches += r;
+  mark();
+  if ((r = launch_pool_cols(g, tb, c->hbuf, c->acc, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "pooling (columns) launch");
+  launches += r;
+  mark();
+  if ((r = launch_counts(g, c->cnt, c->cnt_tmp, c->ncnt, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "window count launch");
+  launches += r;
+  mark();
+  if (what == Out::Emb) {
+    r = launch_gather_emb(ev, K, nK, g, tb, c->acc, c->ncnt, out, c->err, s);
+  } else if (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)) {
+    r = launch_predict_tc(ev, K, nK, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
+  } else {
+    r = launch_predict_fp32(ev, K, nK, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
+    if (r == -2) return fail(VECKM_EUNSUPPORTED, "FP32 perceptron needs 2D*128 floats of shared memory; D=%d is too large", g.D);
+  }
+  if (r < 0) return cuda_fail(cudaGetLastError(), "gather launch");
+  launches += r;
+  mark();
+  if (c->timing) c->pending.push_back(evs);
+  c->last_launches = launches;
+  return VECKM_OK;
+}
+
+bool valid_D(int D) { return D == 64 || D == 128 || D == 192 || D == 256; }
+
+}  // namespace
+
+extern "C" {
+
+const char *veckm_last_error(void) { return g_err; }
+
+void veckm_normals(uint64_t seed, int64_t count, double *h_out) {
+  if (!h_out || count <= 0) return;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int64_t j = 0; 2 * j < count; ++j) {
+    const double u1 = (double)(splitmix64_at(seed, 2 * j) >> 11) * 0x1.0p-53;
+    const double u2 = (double)(splitmix64_at(seed, 2 * j + 1) >> 11) * 0x1.0p-53;
+    const double r = std::sqrt(-2.0 * std::log1p(-u1));
+    h_out[2 * j] = r * std::cos(two_pi * u2);
+    if (2 * j + 1 < count) h_out[2 * j + 1] = r * std::sin(two_pi * u2);
+  }
+}
+
+veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
+  g_err[0] = 0;
+  if (!out || !cfg) return fail(VECKM_EINVAL, "null argument");
+  *out = nullptr;
+  if (cfg->width < 1 || cfg->width > 32767 || cfg->height < 1 || cfg->height > 32767)
+    return fail(VECKM_EINVAL, "sensor size %dx%d outside 1..32767", cfg->width, cfg->height);
+  if (!valid_D(cfg->D)) return fail(VECKM_EINVAL, "D=%d not in {64,128,192,256}", cfg->D);
+  if (cfg->dx < 0 || cfg->dx > 64 || cfg->dy < 0 || cfg->dy > 64)
+    return fail(VECKM_EINVAL, "window radii (%d,%d) outside 0..64", cfg->dx, cfg->dy);
+  if (cfg->hidden != 128) return fail(VECKM_EINVAL, "hidden=%d; this build supports 128", cfg->hidden);
+  // the pooling walker keeps one window of D/2 float4 units per lane in shared memory
+  if ((size_t)(2 * std::max(cfg->dx, cfg->dy) + 1) * (cfg->D / 2) * 16 > 200 * 1024)
+    return fail(VECKM_EUNSUPPORTED, "window %dx%d too large for D=%d", 2 * cfg->dx + 1,
+                2 * cfg->dy + 1, cfg->D);
+  if (cfg->dt_us <= 0) return fail(VECKM_EINVAL, "dt_us must be positive");
+  const int64_t span = cfg->t_span_us > 0 ? cfg->t_span_us : 2 * cfg->dt_us;
+  if (span >= ((int64_t)1 << 32)) return fail(VECKM_EINVAL, "t_span_us too large");
+  if (!cfg->h_W1 || !cfg->h_b1 || !cfg->h_W2 || !cfg->h_b2)
+    return fail(VECKM_EINVAL, "perceptron weights are required");
+  const uint32_t known = VECKM_MLP_BF16 | VECKM_MLP_FP16;
+  if ((cfg->flags & ~known) || ((cfg->flags & VECKM_MLP_BF16) && (cfg->flags & VECKM_MLP_FP16)))
+    return fail(VECKM_EINVAL, "bad flags 0x%x", cfg->flags);
+  if ((cfg->flags & known) && cfg->D > 128)
+    return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
+
+  veckm_ctx *c = new (std::nothrow) veckm_ctx();
+  if (!c) return fail(VECKM_ENOMEM, "host allocation");
+  cudaGetDevice(&c->device);
+  Geometry &g = c->g;
+  g.W = cfg->width; g.H = cfg->height; g.D = cfg->D; g.U = cfg->D / 2;
+  g.dx = cfg->dx; g.dy = cfg->dy;
+  c->hidden = cfg->hidden;
+  c->flags = cfg->flags;
+  c->dt_us = cfg->dt_us;
+  c->t_span = span;
+  c->sigma2 = cfg->sigma2 > 0 ? cfg->sigma2 : 25.0;
+  const int D = g.D;
+  c->T.resize(D); c->X.resize(D); c->Y.resize(D);
+  if (cfg->h_T && cfg->h_X && cfg->h_Y) {
+    std::copy(cfg->h_T, cfg->h_T + D, c->T.begin());
+    std::copy(cfg->h_X, cfg->h_X + D, c->X.begin());
+    std::copy(cfg->h_Y, cfg->h_Y + D, c->Y.begin());
+  } else if (cfg->h_T || cfg->h_X || cfg->h_Y) {
+    delete c;
+    return fail(VECKM_EINVAL, "give all of h_T, h_X, h_Y or none");
+  } else {
+    const double sd = std::sqrt(c->sigma2);
+    veckm_normals(cfg->freq_seed, D, c->T.data());
+    veckm_normals(cfg->freq_seed + 1, D, c->X.data());
+    veckm_normals(cfg->freq_seed + 2, D, c->Y.data());
+    for (int d = 0; d < D; ++d) { c->T[d] *= sd; c->X[d] *= sd; c->Y[d] *= sd; }
+  }
+  // tables
+  const double wx = cfg->dx > 0 ? 1.0 / cfg->dx : 0.0, wy = cfg->dy > 0 ? 1.0 / cfg->dy : 0.0;
+  const double wt = 1.0 / (double)cfg->dt_us;
+  c->nhi = (int)((span >> kTLoBits) + 1);
+  std::vector<float> htx = phase_rows(c->X, wx, g.W, 1);
+  std::vector<float> hty = phase_rows(c->Y, wy, g.H, 1);
+  std::vector<float> hlo = phase_rows(c->T, wt, kTLo, 1);
+  std::vector<float> hhi = phase_rows(c->T, wt, c->nhi, kTLo);
+  const int IN = 2 * D;
+  c->hW1.assign(cfg->h_W1, cfg->h_W1 + (size_t)c->hidden * IN);
+  std::vector<float> hW1t((size_t)IN * c->hidden);
+  for (int h = 0; h < c->hidden; ++h)
+    for (int k = 0; k < IN; ++k) hW1t[(size_t)k * c->hidden + h] = c->hW1[(size_t)h * IN + k];
+  std::vector<uint16_t> hW1h = w1_core_matrix(c->hW1, c->hidden, IN, (c->flags & VECKM_MLP_FP16) != 0);
+
+  const size_t P = (size_t)g.W * g.H;
+  cudaError_t e = cudaSuccess;
+#define VK_TRY(expr)                    \
+  do {                                  \
+    if (e == cudaSuccess) e = (expr);   \
+  } while (0)
+  VK_TRY(dalloc(&c->tx, (size_t)g.W * g.U));
+  VK_TRY(dalloc(&c->ty, (size_t)g.H * g.U));
+  VK_TRY(dalloc(&c->tt_lo, (size_t)kTLo * g.U));
+  VK_TRY(dalloc(&c->tt_hi, (size_t)c->nhi * g.U));
+  VK_TRY(dalloc(&c->W1, (size_t)c->hidden * IN));
+  VK_TRY(dalloc(&c->W1t, (size_t)c->hidden * IN));
+  VK_TRY(dalloc(&c->W1h, (size_t)c->hidden * IN));
+  VK_TRY(dalloc(&c->b1, (size_t)c->hidden));
+  VK_TRY(dalloc(&c->W2, (size_t)2 * c->hidden));
+  VK_TRY(dalloc(&c->b2, 2));
+  VK_TRY(dalloc(&c->acc, P * g.U));
+  VK_TRY(dalloc(&c->hbuf, P * g.U));
+  VK_TRY(dalloc(&c->cnt, P));
+  VK_TRY(dalloc(&c->cnt_tmp, P));
+  VK_TRY(dalloc(&c->ncnt, P));
+  VK_TRY(dalloc(&c->err, 1));
+  VK_TRY(cudaMallocHost(reinterpret_cast<void **>(&c->h_err), sizeof(int)));
+  VK_TRY(cudaMemcpy(c->tx, htx.data(), htx.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->ty, hty.data(), hty.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->tt_lo, hlo.data(), hlo.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->tt_hi, hhi.data(), hhi.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->W1, c->hW1.data(), c->hW1.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->W1t, hW1t.data(), hW1t.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->W1h, hW1h.data(), hW1h.size() * 2, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->b1, cfg->h_b1, (size_t)c->hidden * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->W2, cfg->h_W2, (size_t)2 * c->hidden * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->b2, cfg->h_b2, 2 * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemset(c->err, 0, sizeof(int)));
+#undef VK_TRY
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return cuda_fail(e, "veckm_create");
+  }
+  *out = c;
+  return VECKM_OK;
+}
+
+void veckm_destroy(veckm_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_all(c);
+  delete c;
+}
+
+veckm_status veckm_set_mlp_mode(veckm_ctx *c, uint32_t flags) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  const uint32_t known = VECKM_MLP_BF16 | VECKM_MLP_FP16;
+  if ((flags & ~known) || ((flags & VECKM_MLP_BF16) && (flags & VECKM_MLP_FP16)))
+    return fail(VECKM_EINVAL, "bad flags 0x%x", flags);
+  if ((flags & known) && c->g.D > 128)
+    return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
+  if (flags & known) {
+    std::vector<uint16_t> h = w1_core_matrix(c->hW1, c->hidden, 2 * c->g.D, (flags & VECKM_MLP_FP16) != 0);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c->W1h, h.data(), h.size() * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "veckm_set_mlp_mode");
+  }
+  c->flags = flags;
+  return VECKM_OK;
+}
+
+veckm_status veckm_encode(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_t *t,
+                          int64_t n, uint32_t t_ref, const int64_t *K, int64_t nK, float *emb,
+                          void *stream) {
+  return run(c, x, y, t, n, t_ref, K, nK, emb, (cudaStream_t)stream, Out::Emb);
+}
+
+veckm_status veckm_predict(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_t *t,
+                           int64_t n, uint32_t t_ref, const int64_t *K, int64_t nK, float *flow,
+                           void *stream) {
+  return run(c, x, y, t, n, t_ref, K, nK, flow, (cudaStream_t)stream, Out::Flow);
+}
+
+veckm_status veckm_sync_status(veckm_ctx *c, void *stream) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(c->h_err, c->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "veckm_sync_status");
+  const int w = *c->h_err;
+  if (w & ERR_TIMEOUT) return fail(VECKM_ETIMEOUT, "a bounded device wait ran out");
+  if (w & (ERR_EVENT_RANGE | ERR_INDEX_RANGE))
+    return fail(VECKM_ERANGE, "%s%s", (w & ERR_EVENT_RANGE) ? "event outside the sensor or time span; " : "",
+                (w & ERR_INDEX_RANGE) ? "index in K outside [0, n)" : "");
+  return VECKM_OK;
+}
+
+veckm_status veckm_predict_host(veckm_ctx *c, const int16_t *hx, const int16_t *hy,
+                                const uint32_t *ht, int64_t n, uint32_t t_ref,
+                                const int64_t *hK, int64_t nK, float *hflow, void *stream) {
+  veckm_status st = check_events_args(c, hx, hy, ht, n, hK, nK, hflow);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bx = al(n * 2), by = al(n * 2), bt = al(n * 4), bk = hK ? al(nK * 8) : 0,
+               bf = al(nK * 8);
+  const size_t need = bx + by + bt + bk + bf;
+  if (need > c->st_cap) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (c->st_buf) cudaFree(c->st_buf);
+    c->st_buf = nullptr;
+    c->st_cap = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&c->st_buf, need);
+    if (e != cudaSuccess) return cuda_fail(e, "staging buffers");
+    c->st_cap = need;
+  }
+  char *b = (char *)c->st_buf;
+  int16_t *dx = (int16_t *)b;
+  int16_t *dy = (int16_t *)(b + bx);
+  uint32_t *dt = (uint32_t *)(b + bx + by);
+  int64_t *dK = hK ? (int64_t *)(b + bx + by + bt) : nullptr;
+  float *df = (float *)(b + bx + by + bt + bk);
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    e = cudaMemcpyAsync(dx, hx, n * 2, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy, n * 2, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, ht, n * 4, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && hK && nK > 0) e = cudaMemcpyAsync(dK, hK, nK * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  st = veckm_predict(c, dx, dy, dt, n, t_ref, dK, nK, df, stream);
+  if (st) return st;
+  if (nK > 0) {
+    e = cudaMemcpyAsync(hflow, df, nK * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  }
+  return veckm_sync_status(c, stream);
+}
+
+veckm_status veckm_get_frequencies(const veckm_ctx *c, double *T, double *X, double *Y) {
+  if (!c || !T || !X || !Y) return fail(VECKM_EINVAL, "null argument");
+  std::copy(c->T.begin(), c->T.end(), T);
+  std::copy(c->X.begin(), c->X.end(), X);
+  std::copy(c->Y.begin(), c->Y.end(), Y);
+  return VECKM_OK;
+}
+
+veckm_status veckm_set_timing(veckm_ctx *c, int enable) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  c->timing = enable != 0;
+  return VECKM_OK;
+}
+
+veckm_status veckm_stage_times(veckm_ctx *c, double *ms, int64_t *launches, int nstage) {
+  if (!c || !ms || nstage < 1) return fail(VECKM_EINVAL, "bad argument");
+  for (auto &evs : c->pending) {
+    if (evs.size() == kStages + 1) {
+      cudaError_t e = cudaEventSynchronize(evs.back());
+      if (e != cudaSuccess) return cuda_fail(e, "timing events");
+      for (int i = 0; i < kStages; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, evs[i], evs[i + 1]);
+        c->stage_ms[i] += t;
+        c->stage_launch[i] += 1;
+      }
+    }
+    for (cudaEvent_t e : evs) c->ev_free.push_back(e);
+  }
+  c->pending.clear();
+  for (int i = 0; i < nstage && i < kStages; ++i) {
+    ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->stage_launch[i];
+    c->stage_ms[i] = 0;
+    c->stage_launch[i] = 0;
+  }
+  return VECKM_OK;
+}
+
+int veckm_last_launch_count(const veckm_ctx *c) { return c ? c->last_launches : 0; }
+
+}  // extern "C"

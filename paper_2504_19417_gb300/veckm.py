@@ -1,0 +1,245 @@
+"""Python binding of the C ABI in include/veckm.h (argument marshalling only).
+
+Every step of the encoder and the flow head runs in the CUDA library
+libveckm.so; this module only converts tensors to pointers and sizes and
+passes the caller's CUDA stream.  PyTorch supplies device memory and streams.
+There is no CPU fallback: if the library is missing or fails to load, the
+import of this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+VECKM_OK, VECKM_EINVAL, VECKM_ENOMEM, VECKM_ECUDA = 0, -1, -2, -3
+VECKM_ERANGE, VECKM_ETIMEOUT, VECKM_EBUSY, VECKM_EUNSUPPORTED = -4, -5, -6, -7
+MLP_FP32, MLP_BF16, MLP_FP16 = 0, 1, 2
+STAGES = ("clear", "scatter", "pool_rows", "pool_cols", "counts", "gather")
+
+_STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ERANGE", -5: "ETIMEOUT",
+           -6: "EBUSY", -7: "EUNSUPPORTED"}
+
+
+class VeckmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"veckm {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("D", C.c_int32),
+                ("dx", C.c_int32), ("dy", C.c_int32), ("hidden", C.c_int32),
+                ("dt_us", C.c_int64), ("t_span_us", C.c_int64), ("sigma2", C.c_double),
+                ("freq_seed", C.c_uint64), ("h_T", C.c_void_p), ("h_X", C.c_void_p),
+                ("h_Y", C.c_void_p), ("h_W1", C.c_void_p), ("h_b1", C.c_void_p),
+                ("h_W2", C.c_void_p), ("h_b2", C.c_void_p), ("flags", C.c_uint32)]
+
+
+EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_predict",
+           "veckm_predict_host", "veckm_set_mlp_mode", "veckm_sync_status", "veckm_last_error",
+           "veckm_get_frequencies", "veckm_set_timing", "veckm_stage_times",
+           "veckm_last_launch_count", "veckm_normals")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: Optional[str] = None) -> C.CDLL:
+    """Load libveckm.so (building it first if needed) and declare its signatures."""
+    path = path or _build.build()
+    lib = C.CDLL(path)
+    P, i64, u32, i32 = C.c_void_p, C.c_int64, C.c_uint32, C.c_int
+    lib.veckm_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(_Config)]
+    lib.veckm_destroy.argtypes = [P]
+    lib.veckm_destroy.restype = None
+    ev = [P, P, P, P, i64, u32, P, i64, P, P]
+    lib.veckm_encode.argtypes = ev
+    lib.veckm_predict.argtypes = ev
+    lib.veckm_predict_host.argtypes = ev
+    lib.veckm_set_mlp_mode.argtypes = [P, u32]
+    lib.veckm_sync_status.argtypes = [P, P]
+    lib.veckm_last_error.restype = C.c_char_p
+    lib.veckm_get_frequencies.argtypes = [P, P, P, P]
+    lib.veckm_set_timing.argtypes = [P, i32]
+    lib.veckm_stage_times.argtypes = [P, P, P, i32]
+    lib.veckm_last_launch_count.argtypes = [P]
+    lib.veckm_normals.argtypes = [C.c_uint64, i64, P]
+    lib.veckm_normals.restype = None
+    for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
+                 "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
+                 "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count"):
+        getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise VeckmError(status, lib().veckm_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def normals(seed: int, count: int) -> np.ndarray:
+    out = np.zeros(count, np.float64)
+    lib().veckm_normals(C.c_uint64(seed), count, _np_ptr(out))
+    return out
+
+
+@dataclass
+class Params:
+    width: int
+    height: int
+    D: int = 64
+    dx: int = 10
+    dy: int = 10
+    dt_us: int = 16_000
+    t_span_us: int = 0
+    hidden: int = 128
+    sigma2: float = 25.0
+    freq_seed: int = 0
+
+
+class Encoder:
+    """One veckm context: tables, weights and per-pixel accumulators on the GPU."""
+
+    def __init__(self, p: Params, W1, b1, W2, b2, T=None, X=None, Y=None, mlp_mode: int = MLP_FP32):
+        self.p = p
+        keep = []
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a
+
+        cfg = _Config(width=p.width, height=p.height, D=p.D, dx=p.dx, dy=p.dy, hidden=p.hidden,
+                      dt_us=p.dt_us, t_span_us=p.t_span_us, sigma2=p.sigma2,
+                      freq_seed=p.freq_seed, flags=mlp_mode)
+        for name, a, dt in (("h_T", T, np.float64), ("h_X", X, np.float64),
+                            ("h_Y", Y, np.float64), ("h_W1", W1, np.float32),
+                            ("h_b1", b1, np.float32), ("h_W2", W2, np.float32),
+                            ("h_b2", b2, np.float32)):
+            setattr(cfg, name, _np_ptr(arr(a, dt)))
+        h = C.c_void_p()
+        _check(lib().veckm_create(C.byref(h), C.byref(cfg)))
+        self._h = h
+        self.mlp_mode = mlp_mode
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().veckm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_mlp_mode(self, mode: int):
+        _check(lib().veckm_set_mlp_mode(self._h, mode))
+        self.mlp_mode = mode
+
+    def frequencies(self):
+        D = self.p.D
+        T, X, Y = (np.zeros(D), np.zeros(D), np.zeros(D))
+        _check(lib().veckm_get_frequencies(self._h, _np_ptr(T), _np_ptr(X), _np_ptr(Y)))
+        return T, X, Y
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    @staticmethod
+    def _dev(t, dtype):
+        if t is None:
+            return None
+        assert t.is_cuda and t.dtype == dtype and t.is_contiguous(), (t.device, t.dtype)
+        return C.c_void_p(t.data_ptr()) if t.numel() else None
+
+    def _args(self, x, y, t, K):
+        import torch
+        n = x.numel()
+        nK = n if K is None else K.numel()
+        return (self._dev(x, torch.int16), self._dev(y, torch.int16), self._dev(t, torch.int32),
+                n, self._dev(K, torch.int64), nK)
+
+    def encode(self, x, y, t, t_ref: int, K=None, out=None, stream=None):
+        """emb [nK, 2D] float32 on the device: [Re | Im] per requested event.
+
+        x, y: int16 CUDA tensors; t: int32 CUDA tensor holding the uint32
+        microsecond timestamps bit for bit; K: optional int64 CUDA tensor.
+        """
+        import torch
+        xp, yp, tp, n, Kp, nK = self._args(x, y, t, K)
+        if out is None:
+            out = torch.empty((nK, 2 * self.p.D), dtype=torch.float32, device=x.device)
+        _check(lib().veckm_encode(self._h, xp, yp, tp, n, C.c_uint32(t_ref), Kp, nK,
+                                  self._dev(out, torch.float32), self._stream(stream)))
+        return out
+
+    def predict(self, x, y, t, t_ref: int, K=None, out=None, stream=None):
+        """flow [nK, 2] float32 on the device."""
+        import torch
+        xp, yp, tp, n, Kp, nK = self._args(x, y, t, K)
+        if out is None:
+            out = torch.empty((nK, 2), dtype=torch.float32, device=x.device)
+        _check(lib().veckm_predict(self._h, xp, yp, tp, n, C.c_uint32(t_ref), Kp, nK,
+                                   self._dev(out, torch.float32), self._stream(stream)))
+        return out
+
+    def predict_host(self, x, y, t, t_ref: int, K=None, out=None, stream=None):
+        """Host (CPU, ideally pinned) tensors in, host flows out; synchronising."""
+        import torch
+        n = x.numel()
+        nK = n if K is None else K.numel()
+        if out is None:
+            out = torch.empty((nK, 2), dtype=torch.float32)
+
+        def hp(a):
+            return None if a is None or a.numel() == 0 else C.c_void_p(a.data_ptr())
+        _check(lib().veckm_predict_host(self._h, hp(x), hp(y), hp(t), n, C.c_uint32(t_ref),
+                                        hp(K), nK, hp(out), self._stream(stream)))
+        return out
+
+    def sync_status(self, stream=None):
+        _check(lib().veckm_sync_status(self._h, self._stream(stream)))
+
+    def set_timing(self, on: bool):
+        _check(lib().veckm_set_timing(self._h, 1 if on else 0))
+
+    def stage_times(self):
+        """(milliseconds per stage summed over timed calls, number of timed calls)."""
+        ms = np.zeros(len(STAGES), np.float64)
+        calls = np.zeros(len(STAGES), np.int64)
+        _check(lib().veckm_stage_times(self._h, _np_ptr(ms), _np_ptr(calls), len(STAGES)))
+        return dict(zip(STAGES, ms)), dict(zip(STAGES, calls))
+
+    def last_launch_count(self) -> int:
+        return int(lib().veckm_last_launch_count(self._h))

@@ -1,0 +1,48 @@
+"""Helpers shared by the GPU tests: build a context from seeded inputs, move a
+slice to the device, and the error measures the parity bars are stated in."""
+import numpy as np
+
+from paper_2504_19417_gb300 import synth
+from paper_2504_19417_gb300 import veckm as vk
+
+# Parity bars (derivations in the design notes):
+#  - FP32 encoder: per requested event, ||emb_gpu - emb_ref||_2 / ||emb_ref||_2.
+#  - flows: per event ||flow_gpu - flow_ref||_2 / max(||flow_ref||_2, floor) with
+#    floor = FLOW_FLOOR * median ||flow_ref||_2.
+EMB_TOL_FP32 = 1e-4
+FLOW_TOL_FP32 = 1e-4
+FLOW_TOL = {vk.MLP_FP32: 1e-4, vk.MLP_FP16: 4e-3, vk.MLP_BF16: 2e-2}
+FLOW_FLOOR = 1e-3
+FLOW_FLOOR_HALF = 0.25
+
+
+def make(sl, D, dx=10, dy=10, dt_us=16_000, mode=vk.MLP_FP32, freq_seed=0, t_span_us=None):
+    T, X, Y = synth.frequencies(D, freq_seed)
+    w = synth.mlp_weights(D, 128, 3)
+    span = t_span_us if t_span_us is not None else max(1, int(sl.t.max()) - sl.t_ref if sl.n else 1)
+    p = vk.Params(width=sl.width, height=sl.height, D=D, dx=dx, dy=dy, dt_us=dt_us,
+                  t_span_us=span)
+    enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=mode)
+    return enc, (T, X, Y), w
+
+
+def to_dev(sl):
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(sl.x)).cuda()
+    y = torch.from_numpy(np.ascontiguousarray(sl.y)).cuda()
+    t = torch.from_numpy(np.ascontiguousarray(sl.t).view(np.int32)).cuda()
+    return x, y, t
+
+
+def emb_rel_err(gpu, ref):
+    gpu = np.asarray(gpu, np.float64)
+    num = np.linalg.norm(gpu - ref, axis=1)
+    den = np.linalg.norm(ref, axis=1)
+    return num / den
+
+
+def flow_rel_err(gpu, ref, floor_frac=FLOW_FLOOR):
+    gpu = np.asarray(gpu, np.float64)
+    nr = np.linalg.norm(ref, axis=1)
+    floor = floor_frac * np.median(nr)
+    return np.linalg.norm(gpu - ref, axis=1) / np.maximum(nr, floor)

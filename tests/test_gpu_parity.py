@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Element-by-element comparisons on seeded inputs at sizes the oracle finishes
+in seconds (several tiles of every kernel plus ragged tails), and at the
+benchmark's full sizes on sampled outputs that the oracle computes one by
+one.  Edge cases: empty slices and empty K, a single event, every event on
+one pixel, events on the sensor border, sensors smaller than the window,
+zero window radii, out-of-range events and indices.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_19417_gb300 import synth
+from paper_2504_19417_gb300 import veckm as vk
+from tests.common import (EMB_TOL_FP32, FLOW_FLOOR, FLOW_FLOOR_HALF, FLOW_TOL, emb_rel_err,
+                          flow_rel_err, make, to_dev)
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _oracle_emb(sl, D, dx, dy, dt, TXY, K=None):
+    T, X, Y = TXY
+    return oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D, dx, dy,
+                                float(dt), T, X, Y, K=K)[0]
+
+
+CASES = [
+    # W, H, n, span_us, D, dx, dy, dt_us
+    (346, 260, 20_000, 10_000, 64, 10, 10, 16_000),   # the 346x260 workload, full size
+    (97, 61, 3_000, 30_000, 64, 10, 10, 16_000),       # ragged sensor
+    (200, 150, 8_000, 50_000, 128, 8, 8, 12_000),      # D=128, 17x17 window
+    (64, 40, 2_500, 20_000, 64, 3, 7, 16_000),         # dx != dy
+    (45, 33, 1_500, 5_000, 192, 0, 2, 16_000),         # dx = 0, D=192
+    (15, 9, 600, 10_000, 256, 10, 10, 16_000),         # sensor smaller than the window, D=256
+]
+
+
+@pytest.mark.parametrize("W,H,n,span,D,dx,dy,dt", CASES)
+def test_encode_matches_oracle(W, H, n, span, D, dx, dy, dt):
+    sl = synth.event_slice(W, H, n, span, n_edges=6, frac_noise=0.1, seed=W * 7 + n)
+    enc, TXY, _ = make(sl, D, dx, dy, dt)
+    x, y, t = to_dev(sl)
+    emb = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
+    enc.sync_status()
+    ref = _oracle_emb(sl, D, dx, dy, dt, TXY)
+    err = emb_rel_err(emb, ref)
+    assert err.max() <= EMB_TOL_FP32, (err.max(), np.argmax(err))
+
+
+def test_encode_matches_adjacency_form():
+    sl, D = synth.workload("slice-346x260-20k")
+    enc, TXY, _ = make(sl, D)
+    x, y, t = to_dev(sl)
+    K = np.random.default_rng(0).choice(sl.n, 400, replace=False).astype(np.int64)
+    emb = enc.encode(x, y, t, sl.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
+    T, X, Y = TXY
+    ref, _ = oracle.encode_direct(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D, 10, 10,
+                                  16_000.0, T, X, Y, K=K)
+    assert emb_rel_err(emb, ref).max() <= EMB_TOL_FP32
+
+
+def test_subset_K_with_repeats_equals_rows_of_full():
+    sl = synth.event_slice(120, 90, 5_000, 20_000, seed=5)
+    enc, TXY, _ = make(sl, 64)
+    x, y, t = to_dev(sl)
+    K = np.array([4999, 0, 17, 17, 2500, 3, 3, 3], np.int64)
+    sub = enc.encode(x, y, t, sl.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
+    ref = _oracle_emb(sl, 64, 10, 10, 16_000, TXY, K=K)
+    assert emb_rel_err(sub, ref).max() <= EMB_TOL_FP32
+    assert np.array_equal(sub[2], sub[3]) and np.array_equal(sub[5], sub[7])
+
+
+@pytest.mark.parametrize("mode", [vk.MLP_FP32, vk.MLP_FP16, vk.MLP_BF16])
+@pytest.mark.parametrize("W,H,n,D", [(346, 260, 20_000, 64), (150, 100, 6_000, 128),
+                                     (90, 70, 333, 64)])
+def test_predict_matches_oracle(mode, W, H, n, D):
+    sl = synth.event_slice(W, H, n, 10_000, n_edges=8, seed=n + D)
+    enc, TXY, w = make(sl, D, mode=mode)
+    x, y, t = to_dev(sl)
+    flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+    enc.sync_status()
+    ref = oracle.mlp(_oracle_emb(sl, D, 10, 10, 16_000, TXY), w.W1, w.b1, w.W2, w.b2)
+    floor = FLOW_FLOOR if mode == vk.MLP_FP32 else FLOW_FLOOR_HALF
+    err = flow_rel_err(flow, ref, floor)
+    assert err.max() <= FLOW_TOL[mode], (err.max(), err.mean())
+
+
+def test_switching_precision_keeps_encoder_state():
+    sl = synth.event_slice(100, 80, 4_000, 10_000, seed=77)
+    enc, TXY, w = make(sl, 64, mode=vk.MLP_FP32)
+    x, y, t = to_dev(sl)
+    ref = oracle.mlp(_oracle_emb(sl, 64, 10, 10, 16_000, TXY), w.W1, w.b1, w.W2, w.b2)
+    for mode in (vk.MLP_BF16, vk.MLP_FP16, vk.MLP_FP32):
+        enc.set_mlp_mode(mode)
+        flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+        floor = FLOW_FLOOR if mode == vk.MLP_FP32 else FLOW_FLOOR_HALF
+        assert flow_rel_err(flow, ref, floor).max() <= FLOW_TOL[mode]
+
+
+def test_repeated_calls_clear_accumulators():
+    sl = synth.event_slice(80, 60, 3_000, 10_000, seed=9)
+    enc, TXY, _ = make(sl, 64)
+    x, y, t = to_dev(sl)
+    a = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
+    b = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
+    assert emb_rel_err(b, a).max() < 1e-6
+
+
+def test_single_event_and_one_pixel_closed_forms():
+    D = 64
+    T, X, Y = synth.frequencies(D)
+    w = synth.mlp_weights(D)
+    p = vk.Params(width=32, height=32, D=D, dt_us=16_000, t_span_us=40_000)
+    enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y)
+    x = torch.tensor([31], dtype=torch.int16, device="cuda")
+    y = torch.tensor([0], dtype=torch.int16, device="cuda")
+    t = torch.tensor([123], dtype=torch.int32, device="cuda")
+    e = enc.encode(x, y, t, 100).cpu().numpy()
+    assert np.max(np.abs(e[0, :D] - 1)) < 1e-6 and np.max(np.abs(e[0, D:])) < 1e-6
+    # m events at one pixel: mean of the temporal phases
+    ts = np.array([0, 700, 3100, 9000, 39000], np.uint32)
+    m = ts.size
+    x = torch.full((m,), 7, dtype=torch.int16, device="cuda")
+    y = torch.full((m,), 30, dtype=torch.int16, device="cuda")
+    e = enc.encode(x, y, torch.from_numpy(ts.view(np.int32)).cuda(), 0).cpu().numpy()
+    for k in range(m):
+        want = np.mean(np.exp(1j * np.outer((ts.astype(float) - ts[k]) / 16_000.0, T)), axis=0)
+        got = e[k, :D] + 1j * e[k, D:]
+        assert np.max(np.abs(got - want)) < 2e-6
+
+
+def test_empty_inputs():
+    sl = synth.event_slice(50, 40, 100, 1_000, seed=1)
+    enc, _, _ = make(sl, 64)
+    z16 = torch.empty(0, dtype=torch.int16, device="cuda")
+    z32 = torch.empty(0, dtype=torch.int32, device="cuda")
+    out = enc.encode(z16, z16, z32, 0)
+    assert out.shape == (0, 128)
+    out = enc.predict(z16, z16, z32, 0)
+    assert out.shape == (0, 2)
+    x, y, t = to_dev(sl)
+    out = enc.predict(x, y, t, sl.t_ref, K=torch.empty(0, dtype=torch.int64, device="cuda"))
+    assert out.shape == (0, 2)
+    enc.sync_status()
+
+
+def test_out_of_range_event_reports_erange_and_skips_it():
+    sl = synth.event_slice(60, 50, 2_000, 10_000, seed=3)
+    enc, TXY, _ = make(sl, 64, t_span_us=10_000)
+    xs = sl.x.copy()
+    xs[5] = 60  # off the sensor
+    ts = sl.t.copy()
+    ts[9] = sl.t_ref + 10_001  # beyond the time span
+    xd = torch.from_numpy(xs).cuda()
+    yd = torch.from_numpy(sl.y).cuda()
+    td = torch.from_numpy(ts.view(np.int32)).cuda()
+    emb = enc.encode(xd, yd, td, sl.t_ref).cpu().numpy()
+    with pytest.raises(vk.VeckmError) as ei:
+        enc.sync_status()
+    assert ei.value.status == vk.VECKM_ERANGE
+    enc.sync_status()  # the error word was cleared
+    assert np.all(emb[5] == 0) and np.all(emb[9] == 0)
+    keep = np.setdiff1d(np.arange(sl.n), [5, 9])
+    sub = synth.EventSlice(sl.x[keep], sl.y[keep], sl.t[keep], sl.p[keep], sl.width, sl.height,
+                           sl.t_ref)
+    ref = _oracle_emb(sub, 64, 10, 10, 16_000, TXY)
+    assert emb_rel_err(emb[keep], ref).max() <= EMB_TOL_FP32
+    # an event before the slice start
+    td2 = td.clone()
+    td2[0] = sl.t_ref - 1
+    enc.encode(xd, yd, td2, sl.t_ref)
+    with pytest.raises(vk.VeckmError):
+        enc.sync_status()
+
+
+def test_index_out_of_range_reports_erange():
+    sl = synth.event_slice(60, 50, 500, 10_000, seed=4)
+    x, y, t = to_dev(sl)
+    for mode in (vk.MLP_FP32, vk.MLP_BF16):
+        enc, _, _ = make(sl, 64, mode=mode)
+        K = torch.tensor([0, 500, -1, 7], dtype=torch.int64, device="cuda")
+        f = enc.predict(x, y, t, sl.t_ref, K=K).cpu().numpy()
+        with pytest.raises(vk.VeckmError) as ei:
+            enc.sync_status()
+        assert ei.value.status == vk.VECKM_ERANGE
+        assert np.all(np.isfinite(f))
+
+
+def test_host_entry_point_matches_device_entry_point():
+    sl = synth.event_slice(346, 260, 20_000, 10_000, seed=21)
+    for mode in (vk.MLP_FP32, vk.MLP_BF16):
+        enc, _, _ = make(sl, 64, mode=mode)
+        x, y, t = to_dev(sl)
+        dev = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+        hx = torch.from_numpy(sl.x).pin_memory()
+        hy = torch.from_numpy(sl.y).pin_memory()
+        ht = torch.from_numpy(sl.t.view(np.int32)).pin_memory()
+        host = enc.predict_host(hx, hy, ht, sl.t_ref).numpy()
+        assert flow_rel_err(host, dev.astype(np.float64)).max() < 1e-5
+        K = np.arange(0, sl.n, 7, dtype=np.int64)
+        host_k = enc.predict_host(hx, hy, ht, sl.t_ref, K=torch.from_numpy(K)).numpy()
+        assert flow_rel_err(host_k, dev[K].astype(np.float64)).max() < 1e-5
+
+
+def test_stage_timing_records_every_call():
+    sl = synth.event_slice(100, 80, 4_000, 10_000, seed=2)
+    enc, _, _ = make(sl, 64)
+    x, y, t = to_dev(sl)
+    enc.set_timing(True)
+    for _ in range(3):
+        enc.predict(x, y, t, sl.t_ref)
+    ms, calls = enc.stage_times()
+    assert all(v == 3 for v in calls.values())
+    assert all(v >= 0 for v in ms.values()) and ms["pool_rows"] > 0
+    assert enc.last_launch_count() >= 4
+
+
+@pytest.mark.parametrize("mode", [vk.MLP_BF16, vk.MLP_FP32])
+def test_full_size_640x480_sampled(mode):
+    """The 640x480, 2M-event workload in the launch configuration the benchmark
+    times; the oracle computes a sample of the outputs one by one."""
+    sl, D = synth.workload("slice-640x480-2M")
+    enc, TXY, w = make(sl, D, mode=mode)
+    x, y, t = to_dev(sl)
+    flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+    emb = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
+    enc.sync_status()
+    rng = np.random.default_rng(11)
+    K = np.sort(rng.choice(sl.n, 600, replace=False)).astype(np.int64)
+    ref = _oracle_emb(sl, D, 10, 10, 16_000, TXY, K=K)
+    assert emb_rel_err(emb[K], ref).max() <= EMB_TOL_FP32
+    T, X, Y = TXY
+    Kd = K[::10]
+    refd, _ = oracle.encode_direct(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D, 10, 10,
+                                   16_000.0, T, X, Y, K=Kd)
+    assert emb_rel_err(emb[Kd], refd).max() <= EMB_TOL_FP32
+    fref = oracle.mlp(ref, w.W1, w.b1, w.W2, w.b2)
+    floor = FLOW_FLOOR if mode == vk.MLP_FP32 else FLOW_FLOOR_HALF
+    assert flow_rel_err(flow[K], fref, floor).max() <= FLOW_TOL[mode]
+
+
+def test_full_size_1280x720_d128_sampled():
+    sl, D = synth.workload("slice-1280x720-4M")
+    enc, TXY, w = make(sl, D, mode=vk.MLP_BF16)
+    x, y, t = to_dev(sl)
+    flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+    emb = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
+    enc.sync_status()
+    K = np.sort(np.random.default_rng(12).choice(sl.n, 300, replace=False)).astype(np.int64)
+    ref = _oracle_emb(sl, D, 10, 10, 16_000, TXY, K=K)
+    assert emb_rel_err(emb[K], ref).max() <= EMB_TOL_FP32
+    fref = oracle.mlp(ref, w.W1, w.b1, w.W2, w.b2)
+    assert flow_rel_err(flow[K], fref, FLOW_FLOOR_HALF).max() <= FLOW_TOL[vk.MLP_BF16]
