@@ -110,7 +110,7 @@ def _kernel_traffic(name: str, workload: str):
     src = os.path.join(ROOT, "paper_2504_19417_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".h")):
+        if fn.endswith((".cu", ".h", ".cuh")):
             with open(os.path.join(src, fn), "rb") as f:
                 h.update(f.read())
     digest = h.hexdigest()[:16]
@@ -125,25 +125,27 @@ def source_digest() -> str:
     src = os.path.join(ROOT, "paper_2504_19417_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".h")):
+        if fn.endswith((".cu", ".h", ".cuh")):
             with open(os.path.join(src, fn), "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def algorithmic_bytes(sl, D, nK, touched, touched_K):
-    """Bytes each kernel must move at minimum (one launch), per the model in the
-    design notes: complex FP32 = 8 B per channel, counts 4 B, events 8 B
-    (x, y int16 + t uint32), flows 8 B."""
+    """Bytes each stage must move at minimum (one launch), per the model in the
+    design notes: complex FP32 = 8 B per channel, counts and offsets 4 B,
+    events 8 B (x, y int16 + t uint32), sorted records 12 B (t, index, pixel),
+    flows 8 B."""
     P = sl.width * sl.height
     pix = 8 * D
+    N = sl.n
     return {
-        "clear": P * (pix + 4),
-        "scatter": sl.n * 8 + touched * (pix + 4),
+        "sort": 8 * N + 12 * N + 16 * P,
+        "pixsum": 8 * N + 4 * P + P * pix,
         "pool_rows": 2 * P * pix,
         "pool_cols": 2 * P * pix,
-        "counts": 4 * P * 4,
-        "gather": nK * 8 + touched_K * (pix + 4) + nK * 8,
+        "counts": 16 * P,
+        "gather": 12 * nK + touched_K * (pix + 4) + 8 * nK,
     }
 
 
@@ -208,6 +210,7 @@ def run_ours(args):
     mode = modes[args.mode]
     w_def = dict(synth.WORKLOADS[args.workload])
     w_def["seed"] = w_def["seed"] + 100 * rank  # each rank its own independent slice
+    w_def["n"] = max(1, int(round(w_def["n"] * args.scale)))
     D = w_def.pop("D")
     sl = synth.event_slice(**w_def)
     T, X, Y = synth.frequencies(D, 0)
@@ -389,6 +392,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--lean", action="store_true", help="timed device loop only (for profilers)")
+    ap.add_argument("--scale", type=float, default=1.0, help="events x scale (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=50_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)

@@ -99,7 +99,7 @@ void veckm_destroy(veckm_ctx *ctx);
  *             (then nK must equal n)
  *   d_emb     float [nK][2D] output (device): row i holds Re(emb) for d = 0..D-1
  *             then Im(emb) for d = 0..D-1 of event K[i].
- * n == 0 or nK == 0 is valid and writes nothing. */
+ * nK == 0 is valid (with or without d_K) and does nothing. */
 veckm_status veckm_encode(veckm_ctx *ctx, const int16_t *d_x, const int16_t *d_y,
                           const uint32_t *d_t, int64_t n, uint32_t t_ref_us,
                           const int64_t *d_K, int64_t nK, float *d_emb, void *stream);

@@ -37,6 +37,7 @@ def _sources():
 def _stamp() -> str:
     h = hashlib.sha256()
     for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+            sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
             [os.path.join(ROOT, "include", "veckm.h"), __file__]:
         h.update(p.encode())
         with open(p, "rb") as f:

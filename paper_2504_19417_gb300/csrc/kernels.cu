@@ -1,31 +1,49 @@
-// CUDA-core kernels of the encoder: scatter (Algorithm 1, lines 7-10), the
-// separable window pooling that replaces the adjacency-matrix product (lines
-// 11-20, Eq. 16-17), the gather with the conjugate temporal phase and the
-// division by the window count (line 21), and the plain FP32 perceptron.
+// CUDA-core kernels of the encoder.
+//
+// Pipeline for one slice (Algorithm 1 with the pooling reformulation of
+// Eq. 13-17, Section 2.2.2):
+//   1. k_hist     PixelCount[p] += 1 for every event.
+//   2. k_scan_*   exclusive prefix sum of the counts: each pixel's segment in
+//                 a pixel-sorted event order.
+//   3. k_place    counting-sort placement of a record (t - t_ref, k) for every
+//                 event into its pixel's segment.
+//   4. k_pixsum   PixelEmbed[p] = sum over the segment of exp(i t T/dt), in
+//                 record chunks of equal size; plain stores inside a chunk,
+//                 vector reductions only for the two pixels at its ends.
+//   5. k_box_pass rows, then columns: box sums over the (2dx+1) x (2dy+1)
+//                 window of PixelEmbed modulated by the spatial phase
+//                 exp(i (x X/dx + y Y/dy)) (row pass), demodulated by the
+//                 conjugate phase of the output pixel (column pass).  Because
+//                   sum_q A[q] exp(i (q-p).w) = conj(phi(p)) sum_q A[q] phi(q)
+//                 with phi(q) = exp(i q.w), this equals the window sum with
+//                 the precomputed spatial factors of Eq. 16.
+//   6. k_count_*  window counts n (Eq. 17), exact integer box sums.
+//   7. gather     pooled[p] * conj(exp(i t T/dt)) / n (Eq. 16), fused with the
+//                 perceptron (mlp_tc.cu, or the FP32 kernel below).
 //
 // Layout: a pixel p = y*W + x holds D complex FP32 values interleaved
 // (re, im), channel fastest; float4 unit u of a pixel holds channels 2u and
 // 2u+1.  A warp covers 32 consecutive units (512 bytes) of one pixel, so every
-// per-pixel access below is a fully coalesced 512-byte transaction.
+// per-pixel access is a fully coalesced 512-byte transaction.
 //
-// Phases are never evaluated with trigonometry on the device.  They are
-// products of FP32 table rows that the host computed in FP64:
-//   exp(i t_rel T/dt) = tt_hi[t_rel >> 6] * tt_lo[t_rel & 63]
-//   exp(i x X/dx)     = tx[x],   exp(i y Y/dy) = ty[y].
+// Spatial phases are FP32 table rows computed on the host in FP64,
+// exp(i x X/dx) = tx[x] and exp(i y Y/dy) = ty[y]; the temporal phase
+// exp(i t T/dt) comes from exact fixed-point argument reduction (phase.cuh),
+// so no trigonometric function ever sees an argument outside [-pi, pi).
+// Inside a box-pass block the spatial phase advances by the exact step rows
+// exp(i X/dx), exp(i Y/dy) from a table anchor (at most 2*radius+1 steps, so
+// the recurrence adds at most ~(2r+1) x 1.2e-7 relative error).
 //
-// The pooling uses the modulation identity behind Eq. 16:
-//   sum_q A[q] exp(i (q-p).w) = conj(phi(p)) * sum_q (A[q] phi(q)),
-// phi(q) = exp(i q.w), so the complex 2-D window convolution becomes a
-// plain box sum between a modulation and a demodulation, done as a row pass
-// then a column pass.  Each box sum uses the van Herk / Gil-Werman block
-// scheme (blocks of the window length L; a window is the suffix of one block
-// plus the prefix of the next), so every window sum adds only values inside
-// that window: no running-sum subtraction, whose cancellation next to a
-// dense pixel would destroy the result of a sparse one.
+// Box sums use the van Herk / Gil-Werman block scheme (blocks of the window
+// length L; each window is the suffix of one block plus the prefix of the
+// next), so every window sum adds only values inside that window: there is
+// no running-sum subtraction, whose cancellation next to a dense pixel would
+// destroy the result of a sparse one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "phase.cuh"
 #include "veckm_internal.h"
 
 namespace veckm {
@@ -52,201 +70,407 @@ __device__ __forceinline__ float4 cmul2c(float4 a, float4 b) {
                      fmaf(a.z, b.z, a.w * b.w), fmaf(a.w, b.z, -a.z * b.w));
 }
 
-__device__ __forceinline__ void red_add_v4(float4 *p, float4 v) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w)
-               : "memory");
-}
-
 __device__ __forceinline__ bool event_ok(int x, int y, uint32_t t, const Events &ev, int W, int H,
                                          uint32_t &trel) {
   trel = t - ev.t_ref;
   return x >= 0 && x < W && y >= 0 && y < H && t >= ev.t_ref && trel <= ev.t_span;
 }
 
-// exp(i t_rel T/dt) for unit u: hi row from global (L1-resident; events are
-// time-sorted, so a warp reuses one hi row), lo row from shared memory.
-__device__ __forceinline__ float4 time_phase(const float4 *__restrict__ tt_hi, const float4 *s_lo,
-                                             uint32_t trel, int U, int u) {
-  const float4 hi = __ldg(tt_hi + (size_t)(trel >> kTLoBits) * U + u);
-  const float4 lo = s_lo[(trel & (kTLo - 1)) * U + u];
-  return cmul2(hi, lo);
+// fixed-point frequencies of channels 2u, 2u+1 for each unit this lane owns
+template <int DV>
+__device__ __forceinline__ void load_freqs(const uint2 *__restrict__ wt, int lane, uint2 (&w)[DV][2]) {
+#pragma unroll
+  for (int v = 0; v < DV; ++v) {
+    const int u = lane + 32 * v;
+    w[v][0] = __ldg(wt + 2 * u);
+    w[v][1] = __ldg(wt + 2 * u + 1);
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait0() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
-// Scatter: PixelEmbed[p] += exp(i t T/dt), PixelCount[p] += 1.
-// One warp takes 32 consecutive events; lanes that hit the same pixel are
-// grouped with __match_any_sync, the group's phases are summed in registers
-// and the group issues one vector reduction per unit and one count add.
-template <int DV>
-__global__ void __launch_bounds__(256) k_scatter(Events ev, Geometry g, Tables tb,
-                                                 float4 *__restrict__ acc, int *__restrict__ cnt,
-                                                 int *__restrict__ err) {
-  constexpr int U = 32 * DV;
-  extern __shared__ float4 s_lo[];  // [64][U]
-  for (int i = threadIdx.x; i < kTLo * U; i += blockDim.x) s_lo[i] = tb.tt_lo[i];
-  __syncthreads();
+// 1. counts per pixel; lanes hitting the same pixel add once.
+// In pixel-sorted prediction an invalid event never reaches the perceptron,
+// so its flow row is zeroed here (zero_flow non-null).
+__global__ void __launch_bounds__(256) k_hist(Events ev, Geometry g, int *__restrict__ cnt,
+                                              int *__restrict__ err, float *__restrict__ zero_flow) {
   const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const int64_t nchunks = (ev.n + 31) >> 5;
-  for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks;
-       c += (int64_t)gridDim.x * wpb) {
-    const int64_t k = c * 32 + lane;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ev.n;
+       base += stride) {
+    const int64_t k = base + lane;
+    int key = -1;
+    if (k < ev.n) {
+      uint32_t trel;
+      const int x = ev.x[k], y = ev.y[k];
+      if (event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) {
+        key = y * g.W + x;
+      } else {
+        atomicOr(err, ERR_EVENT_RANGE);
+        if (zero_flow) *reinterpret_cast<float2 *>(zero_flow + 2 * k) = make_float2(0.f, 0.f);
+      }
+    }
+    const unsigned grp = __match_any_sync(kFull, key);
+    if (key >= 0 && (__ffs(grp) - 1) == lane) atomicAdd(cnt + key, __popc(grp));
+  }
+}
+
+// 2. exclusive scan of P counts in blocks of kScanBlock.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += n;
+    }
+    s_warp[lane] = wi - w;  // exclusive
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  const int r = s_warp[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restrict__ cnt, int64_t P,
+                                                              int *__restrict__ bsum) {
+  __shared__ int s_warp[33];
+  const int64_t b0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+  int v = 0;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i)
+    if (b0 + i < P) v += cnt[b0 + i];
+  int total;
+  block_excl_scan(v, s_warp, total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Exclusive scan of the block sums in place (one CTA, any number of blocks).
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int *__restrict__ bsum, int nb,
+                                                           int *__restrict__ total_out) {
+  __shared__ int s_warp[33];
+  int carry = 0;
+  for (int base = 0; base < nb; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? bsum[i] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, s_warp, tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+// off[p] = exclusive prefix, cur[p] = off[p] (placement cursors), off[P] = total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restrict__ cnt, int64_t P,
+                                                             const int *__restrict__ bsum,
+                                                             int *__restrict__ off,
+                                                             int *__restrict__ cur) {
+  __shared__ int s_warp[33];
+  const int64_t b0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+  int c[kScanPer];
+  int v = 0;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    c[i] = (b0 + i < P) ? cnt[b0 + i] : 0;
+    v += c[i];
+  }
+  int total;
+  int run = block_excl_scan(v, s_warp, total) + bsum[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    if (b0 + i < P) {
+      off[b0 + i] = run;
+      cur[b0 + i] = run;
+    }
+    run += c[i];
+  }
+  if (b0 < P && b0 + kScanPer >= P) off[P] = run;  // the thread holding the last pixel
+}
+
+// 3. placement: rec[pos] = (t - t_ref, k), pix[pos] = p.
+__global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__restrict__ cur,
+                                               int2 *__restrict__ rec, int *__restrict__ pix) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ev.n;
+       base += stride) {
+    const int64_t k = base + lane;
     int key = -1;
     uint32_t trel = 0;
     if (k < ev.n) {
       const int x = ev.x[k], y = ev.y[k];
-      if (event_ok(x, y, ev.t[k], ev, g.W, g.H, trel))
-        key = y * g.W + x;
-      else
-        atomicOr(err, ERR_EVENT_RANGE);
+      if (event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) key = y * g.W + x;
     }
     const unsigned grp = __match_any_sync(kFull, key);
-    const bool leader = key >= 0 && (__ffs(grp) - 1) == lane;
-    unsigned todo = __ballot_sync(kFull, leader);
-    while (todo) {
-      const int j = __ffs(todo) - 1;
-      todo &= todo - 1;
-      unsigned members = __shfl_sync(kFull, grp, j);
-      const int pix = __shfl_sync(kFull, key, j);
-      const int m_count = __popc(members);
-      float4 s[DV];
-#pragma unroll
-      for (int v = 0; v < DV; ++v) s[v] = f4zero();
-      while (members) {
-        const int m = __ffs(members) - 1;
-        members &= members - 1;
-        const uint32_t tm = __shfl_sync(kFull, trel, m);
-#pragma unroll
-        for (int v = 0; v < DV; ++v) s[v] = add4(s[v], time_phase(tb.tt_hi, s_lo, tm, U, lane + 32 * v));
-      }
-      float4 *dst = acc + (size_t)pix * U;
-#pragma unroll
-      for (int v = 0; v < DV; ++v) red_add_v4(dst + lane + 32 * v, s[v]);
-      if (lane == 0) atomicAdd(cnt + pix, m_count);
+    const int leader = __ffs(grp) - 1;
+    int pos = 0;
+    if (key >= 0 && leader == lane) pos = atomicAdd(cur + key, __popc(grp));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (key >= 0) {
+      pos += __popc(grp & ((1u << lane) - 1u));
+      rec[pos] = make_int2((int)trel, (int)k);
+      pix[pos] = key;
     }
+  }
+}
+
+// 4. per-pixel phase sums PixelEmbed[p] = sum over the pixel's records of
+// exp(i t T/dt), into an accumulator cleared beforehand (empty pixels stay
+// zero).  Work is balanced by records: warp c takes records
+// [c*kPixRecs, (c+1)*kPixRecs) in pixel-sorted order, streams them in chunks
+// of 32 (t and pixel), and writes each pixel's sum when the pixel changes -
+// a plain store for pixels that lie wholly inside its range, a vector
+// reduction for the first and last pixel, which may continue in a
+// neighbouring warp's range.
+constexpr int kPixRecs = 128;
+
+__device__ __forceinline__ void red_add_v4(float4 *p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+template <int DV>
+__global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int *__restrict__ nsorted,
+                                                const int2 *__restrict__ rec,
+                                                const int *__restrict__ rpix,
+                                                float4 *__restrict__ acc) {
+  constexpr int U = 32 * DV;
+  const int lane = threadIdx.x & 31;
+  const int64_t ns = *nsorted;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  uint2 w[DV][2];
+  load_freqs<DV>(tb.wt, lane, w);
+  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kPixRecs;
+       r0 < ns; r0 += nw * kPixRecs) {
+    const int64_t r1 = r0 + kPixRecs < ns ? r0 + kPixRecs : ns;
+    int sp = -1;        // pixel of the running sum
+    bool first = true;  // the running pixel is the first of this range
+    float4 s[DV];
+#pragma unroll
+    for (int v = 0; v < DV; ++v) s[v] = f4zero();
+    auto write = [&](bool shared) {
+      float4 *dst = acc + (size_t)sp * U + lane;
+#pragma unroll
+      for (int v = 0; v < DV; ++v) {
+        if (shared)
+          red_add_v4(dst + 32 * v, s[v]);
+        else
+          dst[32 * v] = s[v];
+      }
+    };
+    for (int64_t c = r0; c < r1; c += 32) {
+      const int m = (int)(r1 - c < 32 ? r1 - c : 32);
+      const uint32_t tl = lane < m ? (uint32_t)__ldg(&rec[c + lane].x) : 0u;
+      const int pl = lane < m ? __ldg(rpix + c + lane) : 0;
+#pragma unroll 4
+      for (int j = 0; j < m; ++j) {
+        const int pj = __shfl_sync(kFull, pl, j);
+        const uint32_t tj = __shfl_sync(kFull, tl, j);
+        if (pj != sp) {
+          if (sp >= 0) {
+            write(first);
+            first = false;
+          }
+          sp = pj;
+#pragma unroll
+          for (int v = 0; v < DV; ++v) s[v] = f4zero();
+        }
+#pragma unroll
+        for (int v = 0; v < DV; ++v) s[v] = add4(s[v], time_phase2(tj, w[v][0], w[v][1]));
+      }
+    }
+    if (sp >= 0) write(true);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Separable pooling.  One warp walks one line segment (a row segment in the
-// row pass, a column segment in the column pass) with lanes over units.
-// Walker state per lane lives in shared memory: L values, reused as the
-// suffix sums of the current block.
+// 5. box-sum pass.  One warp walks one line segment (a row segment in the row
+// pass, a column segment in the column pass), lanes over units.  Input blocks
+// of L pixels stream into a 3-slot per-warp ring with cp.async (two blocks in
+// flight while the third is consumed); slot contents become the block's
+// suffix sums in place.  Each slot also receives one phase-anchor row.
+//
+// Row pass: input pixel (x, y) is modulated by exp(i (x X/dx + y Y/dy)) before
+// the sum; the x phase advances by the step exp(i X/dx) from an anchor table
+// row loaded once per block (at most L steps from the anchor).
+// Column pass: output pixel (x, y) is demodulated by the conjugate of the
+// same phase, advancing in y from an anchor per output block.
 enum class Pass { Rows, Cols };
 
 template <int DV, Pass P>
-__global__ void __launch_bounds__(128) k_pool_pass(const float4 *__restrict__ src,
-                                                   float4 *__restrict__ dst, Geometry g, Tables tb,
-                                                   int seg, int nseg) {
+__global__ void __launch_bounds__(64) k_box_pass(const float4 *__restrict__ src,
+                                                 float4 *__restrict__ dst, Geometry g, Tables tb,
+                                                 int seg, int nseg) {
   constexpr int U = 32 * DV;
   extern __shared__ float4 smem[];
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
   const int L = 2 * r + 1;
+  const int SL = (L + 1) * U;  // slot: L data rows + 1 anchor row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4 *sv = smem + (size_t)warp * L * U;
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int nlines = (P == Pass::Rows) ? g.H : g.W;
   const int len = (P == Pass::Rows) ? g.W : g.H;
   if (wid >= (int64_t)nlines * nseg) return;
-  const int line = (int)(wid / nseg), s = (int)(wid % nseg);
+  float4 *ring = smem + (size_t)warp * 3 * SL;
+  // neighbouring warps take neighbouring lines of the same segment, so the
+  // blocks in flight at one time sit side by side in memory
+  const int line = (int)(wid % nlines), s = (int)(wid / nlines);
   const int o0 = s * seg;
   const int nout = min(len, o0 + seg) - o0;
   const int in0 = o0 - r;
-  // element pos of this line is at base + pos * stride (float4 units)
   const size_t base = (P == Pass::Rows) ? (size_t)line * g.W * U : (size_t)line * U;
   const size_t stride = (P == Pass::Rows) ? (size_t)U : (size_t)g.W * U;
-  // Row pass: modulate by tx on input; demodulate by conj(tx) and modulate by
-  // ty[line] on output.  Column pass: demodulate by conj(ty) on output.
-  float4 fy[DV];
-  if (P == Pass::Rows) {
+  const int nb = (nout + L - 1) / L;  // output blocks; input blocks 0..nb
+
+  auto slot = [&](int b) { return ring + (size_t)(b % 3) * SL; };
+  auto issue = [&](int b) {  // input block b and its anchor row -> its slot (one group)
+    if (b <= nb) {
+      float4 *sl = slot(b);
+      for (int q = 0; q < L; ++q) {
+        const int pos = in0 + b * L + q;
 #pragma unroll
-    for (int v = 0; v < DV; ++v) fy[v] = __ldg(tb.ty + (size_t)line * U + lane + 32 * v);
-  }
-  auto load = [&](int i, float4(&w)[DV]) {
-    const int pos = in0 + i;
-    if (pos >= 0 && pos < len) {
-#pragma unroll
-      for (int v = 0; v < DV; ++v) {
-        const int u = lane + 32 * v;
-        const float4 a = __ldg(src + base + (size_t)pos * stride + u);
-        w[v] = (P == Pass::Rows) ? cmul2(a, __ldg(tb.tx + (size_t)pos * U + u)) : a;
+        for (int v = 0; v < DV; ++v) {
+          const int u = lane + 32 * v;
+          if (pos >= 0 && pos < len)
+            cp_async16(sl + q * U + u, src + base + (size_t)pos * stride + u);
+          else
+            sl[q * U + u] = f4zero();
+        }
       }
-    } else {
+      const float4 *arow;
+      if (P == Pass::Rows) {  // tx row of the block's first input column (halo rows from -dx)
+        const int a = min(max(in0 + b * L, -g.dx), g.W - 1);
+        arow = tb.tx + (size_t)(a + g.dx) * U;
+      } else {  // ty row of the output block's first row
+        const int a = min(o0 + b * L, g.H - 1);
+        arow = tb.ty + (size_t)a * U;
+      }
 #pragma unroll
-      for (int v = 0; v < DV; ++v) w[v] = f4zero();
+      for (int v = 0; v < DV; ++v) cp_async16(sl + L * U + lane + 32 * v, arow + lane + 32 * v);
     }
+    cp_async_commit();
   };
-  auto emit = [&](int j, const float4(&sum)[DV]) {
-    const int pos = o0 + j;
-#pragma unroll
-    for (int v = 0; v < DV; ++v) {
-      const int u = lane + 32 * v;
-      float4 o;
-      if (P == Pass::Rows)
-        o = cmul2(sum[v], cmul2c(fy[v], __ldg(tb.tx + (size_t)pos * U + u)));
-      else
-        o = cmul2c(sum[v], __ldg(tb.ty + (size_t)pos * U + u));
-      dst[base + (size_t)pos * stride + u] = o;
-    }
-  };
-  // suffix sums of input block 0
-  {
+  auto suffix = [&](float4 *sl) {
     float4 run[DV];
 #pragma unroll
     for (int v = 0; v < DV; ++v) run[v] = f4zero();
     for (int q = L - 1; q >= 0; --q) {
-      float4 w[DV];
-      load(q, w);
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
-        run[v] = add4(run[v], w[v]);
-        sv[q * U + lane + 32 * v] = run[v];
+        run[v] = add4(run[v], sl[q * U + lane + 32 * v]);
+        sl[q * U + lane + 32 * v] = run[v];
       }
     }
-  }
-  const int nb = (nout + L - 1) / L;
-  for (int b = 0; b < nb; ++b) {
-    const int j0 = b * L;
-    {
-      float4 s0[DV];
+  };
+  // fixed factor of this line and the per-step rotation
+  float4 fl[DV], st[DV];
 #pragma unroll
-      for (int v = 0; v < DV; ++v) s0[v] = sv[lane + 32 * v];
-      emit(j0, s0);  // window == block b
+  for (int v = 0; v < DV; ++v) {
+    const int u = lane + 32 * v;
+    if (P == Pass::Rows) {
+      fl[v] = __ldg(tb.ty + (size_t)line * U + u);
+      st[v] = __ldg(tb.sx + u);
+    } else {
+      fl[v] = __ldg(tb.tx + (size_t)(line + g.dx) * U + u);
+      st[v] = __ldg(tb.sy + u);
     }
+  }
+  auto modulate = [&](float4 *sl) {  // row pass: sl[q] *= tx[x0 + q] ty[y]
+    float4 ph[DV];
+#pragma unroll
+    for (int v = 0; v < DV; ++v) ph[v] = cmul2(sl[L * U + lane + 32 * v], fl[v]);
+    for (int q = 0; q < L; ++q) {
+#pragma unroll
+      for (int v = 0; v < DV; ++v) {
+        float4 *e = sl + q * U + lane + 32 * v;
+        *e = cmul2(*e, ph[v]);
+        ph[v] = cmul2(ph[v], st[v]);
+      }
+    }
+  };
+
+  issue(0);
+  issue(1);
+  cp_async_wait1();
+  if (P == Pass::Rows) modulate(slot(0));
+  suffix(slot(0));
+  for (int b = 0; b < nb; ++b) {
+    issue(b + 2);
+    cp_async_wait1();  // block b+1 has landed
+    const float4 *S = slot(b);
+    float4 *V = slot(b + 1);
+    if (P == Pass::Rows && b + 1 <= nb) modulate(V);
+    const int j0 = b * L;
+    float4 dph[DV];  // column pass: phase of the next output, conj applied at emit
+    if (P == Pass::Cols) {
+#pragma unroll
+      for (int v = 0; v < DV; ++v) dph[v] = cmul2(fl[v], S[L * U + lane + 32 * v]);
+    }
+    auto emit = [&](int j, int qs, const float4 *G) {
+      const int pos = o0 + j;
+#pragma unroll
+      for (int v = 0; v < DV; ++v) {
+        const int u = lane + 32 * v;
+        float4 o = S[qs * U + u];
+        if (G) o = add4(o, G[v]);
+        if (P == Pass::Cols) {
+          o = cmul2c(o, dph[v]);
+          dph[v] = cmul2(dph[v], st[v]);
+        }
+        dst[base + (size_t)pos * stride + u] = o;
+      }
+    };
+    emit(j0, 0, nullptr);  // window == block b
     float4 G[DV];
 #pragma unroll
     for (int v = 0; v < DV; ++v) G[v] = f4zero();
-    for (int q = 0; q < L; ++q) {
-      float4 w[DV];
-      load((b + 1) * L + q, w);
+    const int qmax = min(L - 1, nout - 1 - j0);
+    for (int q = 0; q < qmax; ++q) {
 #pragma unroll
-      for (int v = 0; v < DV; ++v) G[v] = add4(G[v], w[v]);
-      if (q + 1 < L && j0 + q + 1 < nout) {
-        float4 o[DV];
-#pragma unroll
-        for (int v = 0; v < DV; ++v) o[v] = add4(sv[(q + 1) * U + lane + 32 * v], G[v]);
-        emit(j0 + q + 1, o);  // suffix of block b from q+1, plus prefix of block b+1 to q
-      }
-#pragma unroll
-      for (int v = 0; v < DV; ++v) sv[q * U + lane + 32 * v] = w[v];
+      for (int v = 0; v < DV; ++v) G[v] = add4(G[v], V[q * U + lane + 32 * v]);
+      emit(j0 + q + 1, q + 1, G);  // suffix of block b from q+1, prefix of block b+1 to q
     }
-    if (b + 1 < nb) {  // suffix sums of block b+1, in place
-      float4 run[DV];
-#pragma unroll
-      for (int v = 0; v < DV; ++v) run[v] = f4zero();
-      for (int q = L - 1; q >= 0; --q) {
-#pragma unroll
-        for (int v = 0; v < DV; ++v) {
-          run[v] = add4(run[v], sv[q * U + lane + 32 * v]);
-          sv[q * U + lane + 32 * v] = run[v];
-        }
-      }
-    }
+    if (b + 1 < nb) suffix(V);
   }
+  cp_async_wait0();
 }
 
-// Window counts (Eq. 17): exact integer box sums, rows then columns.
+// 6. window counts (Eq. 17): exact integer box sums, rows then columns.
 __global__ void k_count_rows(const int *__restrict__ cnt, int *__restrict__ out, int W, int H,
                              int dx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,12 +493,11 @@ __global__ void k_count_cols(const int *__restrict__ rows, int *__restrict__ out
 }
 
 // ---------------------------------------------------------------------------
-// Gather for one event: pooled[p] * conj(exp(i t T/dt)) / n_p.  Returns false
-// (and zeros) for an invalid index or event.
+// 7a. gather for requested events given by index (K, or all in input order):
+// pooled[p] * conj(exp(i t T/dt)) / n_p.  Zeros for an invalid index or event.
 template <int DV>
 __device__ __forceinline__ bool gather_event(const Events &ev, const int64_t *__restrict__ K,
-                                             int64_t nK, int64_t i, const Geometry &g,
-                                             const Tables &tb, const float4 *s_lo,
+                                             int64_t i, const Geometry &g, const uint2 (&w)[DV][2],
                                              const float4 *__restrict__ pooled,
                                              const int *__restrict__ ncnt, int lane,
                                              float4 (&e)[DV], int *err) {
@@ -291,15 +514,13 @@ __device__ __forceinline__ bool gather_event(const Events &ev, const int64_t *__
   }
   const int x = ev.x[k], y = ev.y[k];
   uint32_t trel;
-  if (!event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) return false;  // flagged by the scatter
+  if (!event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) return false;  // flagged by k_hist
   const int pix = y * g.W + x;
   const float inv = 1.0f / (float)__ldg(ncnt + pix);
 #pragma unroll
   for (int v = 0; v < DV; ++v) {
     const int u = lane + 32 * v;
-    const float4 pv = __ldg(pooled + (size_t)pix * U + u);
-    const float4 ph = time_phase(tb.tt_hi, s_lo, trel, U, u);
-    float4 o = cmul2c(pv, ph);
+    float4 o = cmul2c(__ldg(pooled + (size_t)pix * U + u), time_phase2(trel, w[v][0], w[v][1]));
     o.x *= inv; o.y *= inv; o.z *= inv; o.w *= inv;
     e[v] = o;
   }
@@ -312,16 +533,14 @@ __global__ void __launch_bounds__(256) k_gather_emb(Events ev, const int64_t *__
                                                     const float4 *__restrict__ pooled,
                                                     const int *__restrict__ ncnt,
                                                     float *__restrict__ emb, int *err) {
-  constexpr int U = 32 * DV;
-  extern __shared__ float4 s_lo[];
-  for (int i = threadIdx.x; i < kTLo * U; i += blockDim.x) s_lo[i] = tb.tt_lo[i];
-  __syncthreads();
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   const int D = g.D;
+  uint2 w[DV][2];
+  load_freqs<DV>(tb.wt, lane, w);
   for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < nK;
        i += (int64_t)gridDim.x * wpb) {
     float4 e[DV];
-    gather_event<DV>(ev, K, nK, i, g, tb, s_lo, pooled, ncnt, lane, e, err);
+    gather_event<DV>(ev, K, i, g, w, pooled, ncnt, lane, e, err);
     float *row = emb + (size_t)i * 2 * D;
 #pragma unroll
     for (int v = 0; v < DV; ++v) {
@@ -332,28 +551,32 @@ __global__ void __launch_bounds__(256) k_gather_emb(Events ev, const int64_t *__
   }
 }
 
-// ---------------------------------------------------------------------------
-// Plain FP32 perceptron fused with the gather.  A CTA takes 64 events: the
-// 8 warps gather their rows into shared memory, then thread (eg, hg) computes
-// a 4-event x 8-hidden block of the first layer from W1^T in shared memory,
-// applies bias and ReLU, reduces its share of the second layer and the 16
-// threads of an event group combine their partial outputs with shuffles.
+// 7b. plain FP32 perceptron fused with the gather.  A CTA takes 64 requested
+// events: its 8 warps gather rows into shared memory, then thread (eg, hg)
+// computes a 4-event x 8-hidden block of the first layer from W1^T in shared
+// memory, applies bias and ReLU, reduces its share of the second layer, and
+// the 16 threads of an event group combine partial outputs with shuffles.
+// Sorted mode (rec != nullptr) walks the pixel-sorted records, so
+// consecutive rows mostly share a pooled row (L1 hits).
 constexpr int kHid = 128;
 constexpr int kTM = 64;
+constexpr int64_t kInvalidRow = (int64_t)1 << 62;  // output row whose event was invalid
 
 template <int DV>
 __global__ void __launch_bounds__(256) k_predict_fp32(Events ev, const int64_t *__restrict__ K,
-                                                      int64_t nK, Geometry g, Tables tb,
-                                                      const float4 *__restrict__ pooled,
+                                                      int64_t nK, const int2 *__restrict__ rec,
+                                                      const int *__restrict__ rpix,
+                                                      const int *__restrict__ nsorted, Geometry g,
+                                                      Tables tb, const float4 *__restrict__ pooled,
                                                       const int *__restrict__ ncnt, MLP mlp,
                                                       float *__restrict__ flow, int *err) {
   constexpr int U = 32 * DV, IN = 4 * U, LDE = IN + 4;
   extern __shared__ float4 smem4[];
-  const float4 *s_lo = tb.tt_lo;  // low time table read through L1 (shared memory holds W1^T)
-  float *sW = reinterpret_cast<float *>(smem4);           // [IN][kHid]
-  float *sE = sW + IN * kHid;                             // [kTM][LDE]
-  float *sB1 = sE + kTM * LDE;                            // [kHid]
-  float *sW2 = sB1 + kHid;                                // [2][kHid]
+  float *sW = reinterpret_cast<float *>(smem4);  // [IN][kHid]
+  float *sE = sW + IN * kHid;                     // [kTM][LDE]
+  float *sB1 = sE + kTM * LDE;                    // [kHid]
+  float *sW2 = sB1 + kHid;                        // [2][kHid]
+  int64_t *sK = reinterpret_cast<int64_t *>(sW2 + 2 * kHid);  // [kTM] output rows
   for (int i = threadIdx.x; i < IN * kHid / 4; i += blockDim.x)
     reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(mlp.W1t) + i);
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
@@ -366,17 +589,37 @@ __global__ void __launch_bounds__(256) k_predict_fp32(Events ev, const int64_t *
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int eg = threadIdx.x >> 4, hg = threadIdx.x & 15;
   const int D = g.D;
+  const int64_t ns = rec ? (int64_t)*nsorted : nK;
+  uint2 w[DV][2];
+  load_freqs<DV>(tb.wt, lane, w);
   for (int64_t tile = blockIdx.x; tile * kTM < nK; tile += gridDim.x) {
     for (int rr = 0; rr < kTM / 8; ++rr) {
       const int row = warp * (kTM / 8) + rr;
       const int64_t i = tile * kTM + row;
       float4 e[DV];
-      if (i < nK)
-        gather_event<DV>(ev, K, nK, i, g, tb, s_lo, pooled, ncnt, lane, e, err);
-      else {
 #pragma unroll
-        for (int v = 0; v < DV; ++v) e[v] = f4zero();
+      for (int v = 0; v < DV; ++v) e[v] = f4zero();
+      int64_t outk = -1;
+      if (i < ns) {
+        if (rec) {
+          const int2 r = __ldg(rec + i);
+          const int p = __ldg(rpix + i);
+          const float inv = 1.0f / (float)__ldg(ncnt + p);
+#pragma unroll
+          for (int v = 0; v < DV; ++v) {
+            const int u = lane + 32 * v;
+            float4 o = cmul2c(__ldg(pooled + (size_t)p * U + u),
+                              time_phase2((uint32_t)r.x, w[v][0], w[v][1]));
+            o.x *= inv; o.y *= inv; o.z *= inv; o.w *= inv;
+            e[v] = o;
+          }
+          outk = r.y;
+        } else {
+          const bool ok = gather_event<DV>(ev, K, i, g, w, pooled, ncnt, lane, e, err);
+          outk = ok ? i : (i | kInvalidRow);
+        }
       }
+      if (lane == 0) sK[row] = outk;
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
         const int u = lane + 32 * v;
@@ -424,49 +667,54 @@ __global__ void __launch_bounds__(256) k_predict_fp32(Events ev, const int64_t *
     if (hg == 0) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int64_t idx = tile * kTM + 4 * eg + i;
-        if (idx < nK)
-          *reinterpret_cast<float2 *>(flow + 2 * idx) = make_float2(o[i][0] + b20, o[i][1] + b21);
+        const int64_t k = sK[4 * eg + i];
+        if (k >= 0) {
+          const bool ok = !(k & kInvalidRow);
+          *reinterpret_cast<float2 *>(flow + 2 * (k & ~kInvalidRow)) =
+              ok ? make_float2(o[i][0] + b20, o[i][1] + b21) : make_float2(0.f, 0.f);
+        }
       }
     }
     __syncthreads();
   }
 }
 
+// Large dynamic shared memory, and a carveout that lets several CTAs share an SM.
 template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int DV>
-int scatter_impl(const Events &ev, const Geometry &g, const Tables &tb, float4 *acc, int *cnt,
-                 int *err, cudaStream_t s) {
-  if (ev.n == 0) return 0;
-  const size_t sm = (size_t)kTLo * 32 * DV * sizeof(float4);
-  if (set_smem(k_scatter<DV>, sm) != cudaSuccess) return -1;
-  const int64_t nchunks = (ev.n + 31) / 32;
-  const int64_t want = (nchunks + 7) / 8;
-  const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * 6);
-  k_scatter<DV><<<grid, 256, sm, s>>>(ev, g, tb, acc, cnt, err);
+int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
+                const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
+  const int64_t P = (int64_t)g.W * g.H;
+  if (cudaMemsetAsync(acc, 0, (size_t)P * g.U * sizeof(float4), s) != cudaSuccess) return -1;
+  if (n == 0) return 0;
+  const int64_t warps = (n + kPixRecs - 1) / kPixRecs;
+  const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
+  k_pixsum<DV><<<grid, 256, 0, s>>>(g, tb, nsorted, rec, rpix, acc);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <int DV, Pass P>
-int pool_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s) {
+int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s) {
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
   const int L = 2 * r + 1;
   const int len = (P == Pass::Rows) ? g.W : g.H;
   const int nlines = (P == Pass::Rows) ? g.H : g.W;
-  const int seg = L * std::max(1, (96 + L / 2) / L);
+  const int seg = L * std::max(1, (128 + L / 2) / L);
   const int nseg = (len + seg - 1) / seg;
-  const size_t per_warp = (size_t)L * 32 * DV * sizeof(float4);
-  int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
+  const size_t per_warp = (size_t)3 * (L + 1) * 32 * DV * sizeof(float4);
+  const int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
   const size_t sm = per_warp * wpb;
-  if (set_smem(k_pool_pass<DV, P>, sm) != cudaSuccess) return -1;
+  if (set_smem(k_box_pass<DV, P>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const int grid = (int)((warps + wpb - 1) / wpb);
-  k_pool_pass<DV, P><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg);
+  k_box_pass<DV, P><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -474,32 +722,46 @@ template <int DV>
 int gather_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                 const Tables &tb, const float4 *pooled, const int *ncnt, float *emb, int *err,
                 cudaStream_t s) {
-  if (nK == 0) return 0;
-  const size_t sm = (size_t)kTLo * 32 * DV * sizeof(float4);
-  if (set_smem(k_gather_emb<DV>, sm) != cudaSuccess) return -1;
   const int grid = (int)std::min<int64_t>((nK + 7) / 8, (int64_t)num_sms() * 8);
-  k_gather_emb<DV><<<grid, 256, sm, s>>>(ev, K, nK, g, tb, pooled, ncnt, emb, err);
+  k_gather_emb<DV><<<grid, 256, 0, s>>>(ev, K, nK, g, tb, pooled, ncnt, emb, err);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <int DV>
-int predict_fp32_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
-                      const Tables &tb, const float4 *pooled, const int *ncnt, const MLP &mlp,
-                      float *flow, int *err, cudaStream_t s) {
-  if (nK == 0) return 0;
+int predict_fp32_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                      const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb, const float4 *pooled,
+                      const int *ncnt, const MLP &mlp, float *flow, int *err, cudaStream_t s) {
   constexpr int U = 32 * DV, IN = 4 * U;
-  const size_t sm = sizeof(float) * ((size_t)IN * kHid + (size_t)kTM * (IN + 4) + 3 * kHid);
+  const size_t sm = sizeof(float) * ((size_t)IN * kHid + (size_t)kTM * (IN + 4) + 3 * kHid) +
+                    sizeof(int64_t) * kTM;
   if (sm > 227 * 1024) return -2;  // W1^T does not fit in shared memory
   if (set_smem(k_predict_fp32<DV>, sm) != cudaSuccess) return -1;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_predict_fp32<DV>, 256, sm);
+  const int per_sm = blocks_per_sm((const void *)k_predict_fp32<DV>, 256, sm);
   const int64_t tiles = (nK + kTM - 1) / kTM;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * std::max(1, per_sm));
-  k_predict_fp32<DV><<<grid, 256, sm, s>>>(ev, K, nK, g, tb, pooled, ncnt, mlp, flow, err);
+  k_predict_fp32<DV><<<grid, 256, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt,
+                                           mlp, flow, err);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace
+
+int blocks_per_sm(const void *func, int threads, size_t smem) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, func) != cudaSuccess) return 1;
+  int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  const size_t per_block_smem = smem + a.sharedSizeBytes + 1024;  // 1 KB reserved per CTA
+  const int by_smem = (int)(smem_sm / per_block_smem);
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((a.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : 32;
+  const int by_thr = thr_sm / threads;
+  return std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_thr, 32)));
+}
 
 int num_sms() {
   static int n = 0;
@@ -512,28 +774,56 @@ int num_sms() {
   return n;
 }
 
-#define VECKM_DISPATCH_DV(U, CALL)          \
-  switch ((U) / 32) {                       \
+#define VECKM_DISPATCH_DV(U, CALL)                 \
+  switch ((U) / 32) {                              \
     case 1: { constexpr int DV = 1; return CALL; } \
     case 2: { constexpr int DV = 2; return CALL; } \
     case 3: { constexpr int DV = 3; return CALL; } \
     case 4: { constexpr int DV = 4; return CALL; } \
-    default: return -1;                     \
+    default: return -1;                            \
   }
 
-int launch_scatter(const Events &ev, const Geometry &g, const Tables &tb, float4 *acc, int *cnt,
-                   int *err, cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (scatter_impl<DV>(ev, g, tb, acc, cnt, err, s)));
+int launch_hist(const Events &ev, const Geometry &g, int *cnt, int *err, float *zero_flow,
+                cudaStream_t s) {
+  if (ev.n == 0) return 0;
+  const int grid = (int)std::min<int64_t>((ev.n + 255) / 256, (int64_t)num_sms() * 16);
+  k_hist<<<grid, 256, 0, s>>>(ev, g, cnt, err, zero_flow);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int scan_blocks(int64_t P) { return (int)((P + kScanBlock - 1) / kScanBlock); }
+
+int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur, int *total,
+                cudaStream_t s) {
+  const int64_t P = (int64_t)g.W * g.H;
+  const int nb = scan_blocks(P);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(cnt, P, bsum);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb, total);
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(cnt, P, bsum, off, cur);
+  return cudaGetLastError() == cudaSuccess ? 3 : -1;
+}
+
+int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
+                 cudaStream_t s) {
+  if (ev.n == 0) return 0;
+  const int grid = (int)std::min<int64_t>((ev.n + 255) / 256, (int64_t)num_sms() * 16);
+  k_place<<<grid, 256, 0, s>>>(ev, g, cur, rec, pix);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
+                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
+  VECKM_DISPATCH_DV(g.U, (pixsum_impl<DV>(g, tb, nsorted, rec, rpix, n, acc, s)));
 }
 
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
                      cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (pool_pass<DV, Pass::Rows>(g, tb, acc, hbuf, s)));
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Rows>(g, tb, acc, hbuf, s)));
 }
 
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
                      cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (pool_pass<DV, Pass::Cols>(g, tb, hbuf, acc, s)));
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols>(g, tb, hbuf, acc, s)));
 }
 
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s) {
@@ -547,14 +837,17 @@ int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cu
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                       const Tables &tb, const float4 *pooled, const int *ncnt, float *emb,
                       int *err, cudaStream_t s) {
+  if (nK == 0) return 0;
   VECKM_DISPATCH_DV(g.U, (gather_impl<DV>(ev, K, nK, g, tb, pooled, ncnt, emb, err, s)));
 }
 
-int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
-                        const Tables &tb, const float4 *pooled, const int *ncnt, const MLP &mlp,
-                        float *flow, int *err, cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U,
-                    (predict_fp32_impl<DV>(ev, K, nK, g, tb, pooled, ncnt, mlp, flow, err, s)));
+int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                        const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
+                        const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
+                        int *err, cudaStream_t s) {
+  if (nK == 0) return 0;
+  VECKM_DISPATCH_DV(g.U, (predict_fp32_impl<DV>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled,
+                                                ncnt, mlp, flow, err, s)));
 }
 
 }  // namespace veckm

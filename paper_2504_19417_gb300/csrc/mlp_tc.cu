@@ -1,26 +1,35 @@
 // Perceptron on the 5th-generation tensor cores, fused with the gather.
 //
-// For a tile of 128 requested events the CTA gathers emb_k (pooled value at
-// the event's pixel times the conjugate temporal phase over the window count,
-// Algorithm 1 line 21) straight into shared memory as BF16 (or FP16), in the
-// K-major "core matrix" layout that tcgen05.mma reads without swizzle:
-// element (row m, column k) sits at byte
-//     (m / 8) * SBO + (k / 8) * LBO + (m % 8) * 16 + (k % 8) * 2,
-// with LBO = 128 (next 8 columns) and SBO = 16 * K (next 8 rows).  W1 is kept
-// in the same layout (rows = hidden units).  One thread issues K/16 MMAs of
-// shape 128 x 128 x 16 with the FP32 accumulator in tensor memory (128
-// columns), commits them to an mbarrier, and after the (bounded) wait each
-// warp reads its 32 accumulator lanes back with tcgen05.ld, adds b1, applies
-// ReLU and contracts with the 2 x 128 second layer on the CUDA cores.
+// For a tile of 128 requested events the CTA (8 warps) gathers emb_k (the
+// pooled value at the event's pixel times the conjugate temporal phase over
+// the window count, Eq. 16) straight into shared memory as BF16 (or FP16),
+// in the K-major 128-byte-swizzled layout that tcgen05.mma reads: the tile is
+// split into K-blocks of 64 columns; in K-block kb, row m occupies the 128
+// bytes at kb * (128 rows * 128 B) + (m / 8) * 1024 + (m % 8) * 128, and its
+// 16-byte chunk c (columns 8c..8c+7 of the block) sits at chunk position
+// c XOR (m % 8).  A warp writing one row therefore covers 32 distinct banks.
+// W1 is stored the same way (rows = hidden units).  One thread issues 2D/16
+// MMAs of shape 128 x 128 x 16 with the FP32 accumulator in tensor memory
+// (128 columns) and commits them to an mbarrier; after the bounded wait the
+// warps read the accumulator back with tcgen05.ld (warp w reads lane quadrant
+// w % 4, column half w / 4), add b1, apply ReLU and contract with the 2 x 128
+// second layer on the CUDA cores.
 //
-// The first layer is the dense contraction [128 x 2D] x [2D x 128]; the second
-// layer (128 -> 2) is too thin for the tensor cores and stays in registers.
+// Requested events come either in pixel-sorted order (records from the
+// counting sort: consecutive rows mostly share a pooled row; the next tile's
+// rows are prefetched into L2 while this one computes) or by index (an
+// explicit K list, or all events in input order).
+//
+// The first layer is the dense contraction [128 x 2D] x [2D x 128]; the
+// second layer (128 -> 2) is too thin for the tensor cores and stays in
+// registers.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "phase.cuh"
 #include "veckm_internal.h"
 
 namespace veckm {
@@ -30,7 +39,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kM = 128;    // events per tile (MMA M)
 constexpr int kN = 128;    // hidden units (MMA N)
+constexpr int kWarps = 8;
+constexpr int kRowsPerWarp = kM / kWarps;
 constexpr int kTmemCols = 128;
+constexpr int64_t kInvalidRow = (int64_t)1 << 62;  // output row whose event was invalid
 constexpr long long kWaitLimitCycles = 4000000000LL;  // ~2 s at 2 GHz, then give up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -46,14 +58,23 @@ __device__ __forceinline__ float4 cmul2(float4 a, float4 b) {
                      fmaf(a.z, b.z, -a.w * b.w), fmaf(a.z, b.w, a.w * b.z));
 }
 
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, K-major with 128-byte swizzling: start
+// address, stride byte offset 1024 (next group of 8 rows), leading byte
+// offset unused for this layout, fixed version bits 0b001 at 46, swizzle
+// mode 2 (128B) at bits 61-63.  Every swizzle atom starts 1024-aligned.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // fixed 0b001 (descriptor version)
-  // base offset 0, relative LBO, swizzle mode 0 (none)
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
+}
+
+// byte offset of element (r, k) in a K-major SW128 tile of 128 rows
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+  return (uint32_t)((k >> 6) * (128 * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
+                    ((((k >> 3) & 7) ^ (r & 7)) << 4) + (k & 7) * 2);
 }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16 (1) or F16 (0),
@@ -106,28 +127,37 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 template <int DV>
-__global__ void __launch_bounds__(128, 1)
-    k_predict_tc(Events ev, const int64_t *__restrict__ K, int64_t nK, Geometry g, Tables tb,
-                 const float4 *__restrict__ pooled, const int *__restrict__ ncnt, MLP mlp,
-                 float *__restrict__ flow, int *err) {
+__global__ void __launch_bounds__(kWarps * 32, 2)
+    k_predict_tc(Events ev, const int64_t *__restrict__ K, int64_t nK,
+                 const int2 *__restrict__ rec, const int *__restrict__ rpix,
+                 const int *__restrict__ nsorted, Geometry g,
+                 Tables tb, const float4 *__restrict__ pooled, const int *__restrict__ ncnt,
+                 MLP mlp, float *__restrict__ flow, int *err) {
   constexpr int U = 32 * DV;
   constexpr int IN = 4 * U;            // 2D, the MMA K extent
-  constexpr int SBO = 16 * IN;         // bytes between 8-row groups
-  constexpr int LBO = 128;             // bytes between 8-column groups
   constexpr int TILE_BYTES = kM * IN * 2;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *sA = smem;                     // [128 x IN] half, core-matrix layout
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = smem;                     // [128 x IN] half, SW128 layout
   uint8_t *sB = smem + TILE_BYTES;        // [128 x IN] half (W1), same layout
   float *sB1 = reinterpret_cast<float *>(sB + kN * IN * 2);  // [128]
   float *sW2 = sB1 + kN;                                      // [2][128]
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sW2 + 2 * kN);
+  float2 *sPart = reinterpret_cast<float2 *>(sW2 + 2 * kN);   // [128] partial outputs
+  int64_t *sK = reinterpret_cast<int64_t *>(sPart + kM);      // [128] output rows
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sK + kM);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fp16 = mlp.half_kind;
   const int D = g.D;
+  uint2 wf[DV][2];  // fixed-point frequencies of this lane's channels
+#pragma unroll
+  for (int v = 0; v < DV; ++v) {
+    wf[v][0] = __ldg(tb.wt + 2 * (lane + 32 * v));
+    wf[v][1] = __ldg(tb.wt + 2 * (lane + 32 * v) + 1);
+  }
 
-  // W1 (already in core-matrix order), b1, W2 into shared memory.
+  // W1 (already in SW128 order), b1, W2 into shared memory.
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
     uint4 *dst = reinterpret_cast<uint4 *>(sB);
@@ -161,56 +191,99 @@ __global__ void __launch_bounds__(128, 1)
   const float b20 = mlp.b2[0], b21 = mlp.b2[1];
   uint32_t phase = 0;
   bool timed_out = false;
+  const int64_t ns = rec ? (int64_t)*nsorted : nK;
+  // L2 prefetch of the next tile (sorted order): thread tid covers half of
+  // row tid % 128; its pixel index is loaded one tile ahead.
+  const int pf_row = tid & (kM - 1), pf_half = tid >> 7;
+  auto pf_pixel = [&](int64_t t) -> int {
+    const int64_t i = t * kM + pf_row;
+    return (rec && i < ns) ? __ldg(rpix + i) : -1;
+  };
+  int pf_pix = pf_pixel((int64_t)blockIdx.x + gridDim.x);
 
   for (int64_t tile = blockIdx.x; tile * kM < nK; tile += gridDim.x) {
-    // --- gather 32 rows per warp into sA ---------------------------------
+    if (rec) {
+      if (pf_pix >= 0) {
+        const char *row = reinterpret_cast<const char *>(pooled + (size_t)pf_pix * U);
+#pragma unroll
+        for (int l = 0; l < 2 * DV; ++l)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + (pf_half * 2 * DV + l) * 128));
+      }
+      const int64_t nt = tile + 2 * (int64_t)gridDim.x;
+      if (tid < 12 && nt * kM < ns) {  // records (1 KB) and pixels (512 B) of the tile after
+        const char *pr = tid < 8 ? reinterpret_cast<const char *>(rec + nt * kM) + tid * 128
+                                 : reinterpret_cast<const char *>(rpix + nt * kM) + (tid - 8) * 128;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pr));
+      }
+      pf_pix = pf_pixel(tile + 2 * (int64_t)gridDim.x);
+    }
+    // --- gather 16 rows per warp into sA ---------------------------------
     {
-      const int64_t i = tile * kM + warp * 32 + lane;  // this lane's event (metadata)
+      // lane j < 16 holds the metadata of row warp*16 + j
+      const int64_t i = tile * kM + warp * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
       int pix = -1;
       uint32_t trel = 0;
       float inv = 0.f;
-      if (i < nK) {
-        int64_t k = i;
-        bool ok = true;
-        if (K) {
-          k = K[i];
-          if (k < 0 || k >= ev.n) {
-            atomicOr(err, ERR_INDEX_RANGE);
-            ok = false;
+      int64_t outk = -1;
+      if (i < ns) {
+        if (rec) {
+          const int2 r = __ldg(rec + i);
+          pix = __ldg(rpix + i);
+          trel = (uint32_t)r.x;
+          outk = r.y;
+          inv = 1.0f / (float)__ldg(ncnt + pix);
+        } else {
+          int64_t k = i;
+          bool ok = true;
+          if (K) {
+            k = K[i];
+            if (k < 0 || k >= ev.n) {
+              if (lane < kRowsPerWarp) atomicOr(err, ERR_INDEX_RANGE);
+              ok = false;
+            }
           }
-        }
-        if (ok) {
-          const int x = ev.x[k], y = ev.y[k];
-          const uint32_t t = ev.t[k];
-          trel = t - ev.t_ref;
-          if (x >= 0 && x < g.W && y >= 0 && y < g.H && t >= ev.t_ref && trel <= ev.t_span) {
-            pix = y * g.W + x;
-            inv = 1.0f / (float)__ldg(ncnt + pix);
+          if (ok) {
+            const int x = ev.x[k], y = ev.y[k];
+            const uint32_t t = ev.t[k];
+            trel = t - ev.t_ref;
+            if (x >= 0 && x < g.W && y >= 0 && y < g.H && t >= ev.t_ref && trel <= ev.t_span) {
+              pix = y * g.W + x;
+              inv = 1.0f / (float)__ldg(ncnt + pix);
+            }
           }
+          outk = pix >= 0 ? i : (i | kInvalidRow);  // an invalid event's row gets zeros
         }
       }
-#pragma unroll 4
-      for (int j = 0; j < 32; ++j) {
-        const int pj = __shfl_sync(kFull, pix, j);
-        const uint32_t tj = __shfl_sync(kFull, trel, j);
-        const float ij = __shfl_sync(kFull, inv, j);
-        const int m = warp * 32 + j;
-        uint8_t *rowp = sA + (m >> 3) * SBO + (m & 7) * 16;
+      if (lane < kRowsPerWarp) sK[warp * kRowsPerWarp + lane] = outk;
+      // batches of rows: all pooled-row loads of a batch are issued before any
+      // is used; the temporal phase is computed, not loaded
+      constexpr int kB = 8 / DV;
 #pragma unroll
-        for (int v = 0; v < DV; ++v) {
-          const int u = lane + 32 * v;
-          float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (pj >= 0) {
-            const float4 pv = __ldg(pooled + (size_t)pj * U + u);
-            const float4 ph = cmul2(__ldg(tb.tt_hi + (size_t)(tj >> kTLoBits) * U + u),
-                                    __ldg(tb.tt_lo + (size_t)(tj & (kTLo - 1)) * U + u));
-            e = cmul2c(pv, ph);
-            e.x *= ij; e.y *= ij; e.z *= ij; e.w *= ij;
+      for (int j0 = 0; j0 < kRowsPerWarp; j0 += kB) {
+        float4 pv[kB][DV];
+        int pjs[kB];
+#pragma unroll
+        for (int r = 0; r < kB; ++r) {
+          pjs[r] = __shfl_sync(kFull, pix, j0 + r);
+          const int pc = pjs[r] >= 0 ? pjs[r] : 0;
+#pragma unroll
+          for (int v = 0; v < DV; ++v) pv[r][v] = __ldg(pooled + (size_t)pc * U + lane + 32 * v);
+        }
+#pragma unroll
+        for (int r = 0; r < kB; ++r) {
+          const int m = warp * kRowsPerWarp + j0 + r;
+          const float ij = __shfl_sync(kFull, inv, j0 + r);
+          const uint32_t tj = __shfl_sync(kFull, trel, j0 + r);
+          const float sc = pjs[r] >= 0 ? ij : 0.f;
+#pragma unroll
+          for (int v = 0; v < DV; ++v) {
+            const int u = lane + 32 * v;
+            float4 e = cmul2c(pv[r][v], time_phase2(tj, wf[v][0], wf[v][1]));
+            e.x *= sc; e.y *= sc; e.z *= sc; e.w *= sc;
+            // Re of channels 2u, 2u+1 at columns k = 2u, 2u+1; Im at D + 2u, D + 2u + 1
+            *reinterpret_cast<uint32_t *>(sA + sw128_off(m, 2 * u)) = pack2(e.x, e.z, fp16);
+            *reinterpret_cast<uint32_t *>(sA + sw128_off(m, D + 2 * u)) = pack2(e.y, e.w, fp16);
           }
-          // Re of channels 2u, 2u+1 at columns k = 2u, 2u+1; Im at D + 2u, D + 2u + 1
-          const int kr = 2 * u, ki = D + 2 * u;
-          *reinterpret_cast<uint32_t *>(rowp + (kr >> 3) * LBO + (kr & 7) * 2) = pack2(e.x, e.z, fp16);
-          *reinterpret_cast<uint32_t *>(rowp + (ki >> 3) * LBO + (ki & 7) * 2) = pack2(e.y, e.w, fp16);
         }
       }
     }
@@ -222,8 +295,10 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) {
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk) {
-        const uint64_t ad = make_desc(sA_a + kk * 2 * LBO, LBO, SBO);
-        const uint64_t bd = make_desc(sB_a + kk * 2 * LBO, LBO, SBO);
+        // K-step kk: K-block kk / 4, 32-byte step kk % 4 inside the swizzle atom
+        const uint32_t koff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
+        const uint64_t ad = make_desc_sw128(sA_a + koff);
+        const uint64_t bd = make_desc_sw128(sB_a + koff);
         const uint32_t acc = kk > 0 ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -249,23 +324,38 @@ __global__ void __launch_bounds__(128, 1)
     }
     // --- epilogue: bias, ReLU, second layer ----------------------------------
     {
+      const int q = warp & 3, hh = warp >> 2;
+      const int row = q * 32 + lane;
       float o0 = 0.f, o1 = 0.f;
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-      for (int c0 = 0; c0 < kN; c0 += 32) {
+      for (int c0 = hh * (kN / 2); c0 < (hh + 1) * (kN / 2); c0 += 32) {
         float h[32];
         tmem_ld32(lane_base + c0, h);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float a = fmaxf(h[j] + sB1[c0 + j], 0.f);
-          o0 = fmaf(a, sW2[c0 + j], o0);
-          o1 = fmaf(a, sW2[kN + c0 + j], o1);
+        for (int j = 0; j < 32; j += 4) {
+          const float4 bb = *reinterpret_cast<const float4 *>(sB1 + c0 + j);
+          const float4 w0 = *reinterpret_cast<const float4 *>(sW2 + c0 + j);
+          const float4 w1 = *reinterpret_cast<const float4 *>(sW2 + kN + c0 + j);
+          const float a0 = fmaxf(h[j] + bb.x, 0.f), a1 = fmaxf(h[j + 1] + bb.y, 0.f);
+          const float a2 = fmaxf(h[j + 2] + bb.z, 0.f), a3 = fmaxf(h[j + 3] + bb.w, 0.f);
+          o0 = fmaf(a3, w0.w, fmaf(a2, w0.z, fmaf(a1, w0.y, fmaf(a0, w0.x, o0))));
+          o1 = fmaf(a3, w1.w, fmaf(a2, w1.z, fmaf(a1, w1.y, fmaf(a0, w1.x, o1))));
         }
       }
-      const int64_t idx = tile * kM + warp * 32 + lane;
-      if (idx < nK) *reinterpret_cast<float2 *>(flow + 2 * idx) = make_float2(o0 + b20, o1 + b21);
+      if (hh == 1) sPart[row] = make_float2(o0, o1);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (hh == 0) {
+        const float2 pp = sPart[row];
+        const int64_t k = sK[row];
+        if (k >= 0) {
+          const bool ok = !(k & kInvalidRow);
+          *reinterpret_cast<float2 *>(flow + 2 * (k & ~kInvalidRow)) =
+              ok ? make_float2(o0 + pp.x + b20, o1 + pp.y + b21) : make_float2(0.f, 0.f);
+        }
+      }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
@@ -283,33 +373,38 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 template <int DV>
-int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
-                    const Tables &tb, const float4 *pooled, const int *ncnt, const MLP &mlp,
-                    float *flow, int *err, cudaStream_t s) {
+int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                    const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb, const float4 *pooled,
+                    const int *ncnt, const MLP &mlp, float *flow, int *err, cudaStream_t s) {
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
-  const size_t sm = (size_t)2 * kM * IN * 2 + sizeof(float) * 3 * kN + 64;
-  if (sm > 48 * 1024 &&
-      cudaFuncSetAttribute(k_predict_tc<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess)
+  const size_t sm = (size_t)2 * kM * IN * 2 + sizeof(float) * 3 * kN + sizeof(float2) * kM +
+                    sizeof(int64_t) * kM + 64 + 1024;  // + alignment slack for the SW128 atoms
+  if (cudaFuncSetAttribute(k_predict_tc<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_predict_tc<DV>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return -1;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_predict_tc<DV>, 128, sm);
-  per_sm = std::max(1, std::min(per_sm, 512 / kTmemCols));
+  const int per_sm = std::min(blocks_per_sm((const void *)k_predict_tc<DV>, kWarps * 32, sm),
+                              512 / kTmemCols);
   const int64_t tiles = (nK + kM - 1) / kM;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm);
-  k_predict_tc<DV><<<grid, 128, sm, s>>>(ev, K, nK, g, tb, pooled, ncnt, mlp, flow, err);
+  k_predict_tc<DV><<<grid, kWarps * 32, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled,
+                                                 ncnt, mlp, flow, err);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace
 
-int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
-                      const Tables &tb, const float4 *pooled, const int *ncnt, const MLP &mlp,
-                      float *flow, int *err, cudaStream_t s) {
+int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                      const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
+                      const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
+                      int *err, cudaStream_t s) {
   switch (g.U / 32) {
-    case 1: return predict_tc_impl<1>(ev, K, nK, g, tb, pooled, ncnt, mlp, flow, err, s);
-    case 2: return predict_tc_impl<2>(ev, K, nK, g, tb, pooled, ncnt, mlp, flow, err, s);
+    case 1:
+      return predict_tc_impl<1>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
+    case 2:
+      return predict_tc_impl<2>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
     default: return -1;  // 2D > 256 does not fit two operand tiles in shared memory
   }
 }

@@ -42,7 +42,7 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
-constexpr int kStages = 6;  // clear, scatter, pool rows, pool cols, counts, gather
+constexpr int kStages = 6;  // sort, pixel sums, pool rows, pool cols, counts, gather
 
 }  // namespace
 
@@ -55,12 +55,17 @@ struct veckm_ctx {
   double sigma2 = 25.0;
   std::vector<double> T, X, Y;
   // device state
-  float4 *tx = nullptr, *ty = nullptr, *tt_lo = nullptr, *tt_hi = nullptr;
-  int nhi = 0;
+  float4 *tx = nullptr, *ty = nullptr, *sx = nullptr, *sy = nullptr;
+  uint2 *wt = nullptr;
   float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
   uint16_t *W1h = nullptr;
   float4 *acc = nullptr, *hbuf = nullptr;
   int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
+  int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
+  // pixel-sorted event records (grown on demand)
+  int2 *rec = nullptr;
+  int *rpix = nullptr;
+  int64_t rec_cap = 0;
   std::vector<float> hW1;  // host copy (re-encoding on precision switch)
   // staging for the host-buffer entry point
   void *st_buf = nullptr;
@@ -74,7 +79,7 @@ struct veckm_ctx {
   int64_t stage_launch[kStages] = {};
   int last_launches = 0;
 
-  Tables tables() const { return Tables{tx, ty, tt_lo, tt_hi}; }
+  Tables tables() const { return Tables{tx, ty, sx, sy, wt}; }
   MLP mlp() const {
     return MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0};
   }
@@ -87,16 +92,16 @@ cudaError_t dalloc(T **p, size_t count) {
   return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
 }
 
-// exp(i n w_d) for n in [0, rows) as interleaved FP32 (re, im), channel fastest.
-// The angle n * w_d is formed in FP64 (|n w| stays below ~1e6 rad, where FP64
-// keeps ~1e-10 rad), then rounded once to FP32 per component.
-std::vector<float> phase_rows(const std::vector<double> &w, double scale, int64_t rows,
-                              int64_t step) {
+// exp(i (first + n) * step * w_d * scale) for n in [0, rows) as interleaved
+// FP32 (re, im), channel fastest.  The angle is formed in FP64 (it stays below
+// ~1e6 rad, where FP64 keeps ~1e-10 rad), then rounded once to FP32.
+std::vector<float> phase_rows(const std::vector<double> &w, double scale, int64_t first,
+                              int64_t rows, int64_t step) {
   const size_t D = w.size();
   std::vector<float> out((size_t)rows * D * 2);
   for (int64_t n = 0; n < rows; ++n)
     for (size_t d = 0; d < D; ++d) {
-      const double a = (double)(n * step) * (w[d] * scale);
+      const double a = (double)((first + n) * step) * (w[d] * scale);
       out[((size_t)n * D + d) * 2] = (float)std::cos(a);
       out[((size_t)n * D + d) * 2 + 1] = (float)std::sin(a);
     }
@@ -112,21 +117,24 @@ uint16_t half_bits(float v, bool fp16) {
   return *reinterpret_cast<uint16_t *>(&b);
 }
 
-// W1 [hidden][IN] -> core-matrix order used by the tcgen05 kernel:
-// byte (n/8)*16*IN + (k/8)*128 + (n%8)*16 + (k%8)*2.
+// W1 [hidden][IN] -> the K-major 128-byte-swizzled order the tcgen05 kernel
+// reads: K-blocks of 64 columns, each hidden x 128 B; row n of a block at
+// (n/8)*1024 + (n%8)*128, its 16-byte chunk c at position c ^ (n%8).
 std::vector<uint16_t> w1_core_matrix(const std::vector<float> &W1, int hidden, int IN, bool fp16) {
   std::vector<uint16_t> out((size_t)hidden * IN);
   for (int n = 0; n < hidden; ++n)
     for (int k = 0; k < IN; ++k) {
-      const size_t byte = (size_t)(n / 8) * 16 * IN + (size_t)(k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+      const size_t byte = (size_t)(k / 64) * hidden * 128 + (size_t)(n / 8) * 1024 + (n % 8) * 128 +
+                          (size_t)((((k / 8) % 8) ^ (n % 8)) * 16) + (k % 8) * 2;
       out[byte / 2] = half_bits(W1[(size_t)n * IN + k], fp16);
     }
   return out;
 }
 
 void free_all(veckm_ctx *c) {
-  void *ptrs[] = {c->tx, c->ty, c->tt_lo, c->tt_hi, c->W1, c->W1t, c->b1, c->W2, c->b2,
-                  c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf};
+  void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
+                  c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
+                  c->off, c->cur, c->bsum, c->total, c->rec, c->rpix};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -151,7 +159,8 @@ veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const
   if (!c) return fail(VECKM_EINVAL, "null context");
   if (n < 0 || nK < 0) return fail(VECKM_EINVAL, "negative size (n=%lld, nK=%lld)", (long long)n, (long long)nK);
   if (n > 0 && (!x || !y || !t)) return fail(VECKM_EINVAL, "null event buffer with n=%lld", (long long)n);
-  if (!K && nK != n) return fail(VECKM_EINVAL, "K is NULL but nK (%lld) != n (%lld)", (long long)nK, (long long)n);
+  if (!K && nK != n && nK != 0)
+    return fail(VECKM_EINVAL, "K is NULL but nK (%lld) != n (%lld)", (long long)nK, (long long)n);
   if (nK > 0 && !out) return fail(VECKM_EINVAL, "null output buffer");
   if (nK > 0 && n == 0) return fail(VECKM_EINVAL, "nK > 0 with an empty slice");
   if (n >= (int64_t)1 << 31) return fail(VECKM_EINVAL, "n too large (%lld)", (long long)n);
@@ -165,7 +174,7 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
   veckm_status st = check_events_args(c, x, y, t, n, K, nK, out);
   if (st) return st;
   c->last_launches = 0;
-  if (nK == 0 && n == 0) return VECKM_OK;
+  if (nK == 0) return VECKM_OK;  // nothing requested: no work
   const Geometry &g = c->g;
   const Events ev{x, y, t, n, t_ref, (uint32_t)c->t_span};
   const Tables tb = c->tables();
@@ -178,14 +187,36 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
     }
   };
   const size_t P = (size_t)g.W * g.H;
+  // pixel-sorted prediction for "all events"; explicit K keeps input order
+  const bool sorted = (what == Out::Flow) && K == nullptr;
+  if (n > c->rec_cap) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (c->rec) cudaFree(c->rec);
+    if (c->rpix) cudaFree(c->rpix);
+    c->rec = nullptr;
+    c->rpix = nullptr;
+    c->rec_cap = 0;
+    if (e == cudaSuccess) e = dalloc(&c->rec, (size_t)n);
+    if (e == cudaSuccess) e = dalloc(&c->rpix, (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(e, "event record buffers");
+    c->rec_cap = n;
+  }
   int launches = 0, r;
   mark();
-  cudaError_t e = cudaMemsetAsync(c->acc, 0, P * g.U * sizeof(float4), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
-  if (e != cudaSuccess) return cuda_fail(e, "clearing the accumulators");
+  cudaError_t e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the counts");
+  if ((r = launch_hist(ev, g, c->cnt, c->err, sorted ? out : nullptr, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "histogram launch");
+  launches += r;
+  if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "scan launch");
+  launches += r;
+  if ((r = launch_place(ev, g, c->cur, c->rec, c->rpix, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "placement launch");
+  launches += r;
   mark();
-  if ((r = launch_scatter(ev, g, tb, c->acc, c->cnt, c->err, s)) < 0)
-    return cuda_fail(cudaGetLastError(), "scatter launch");
+  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s)) < 0)
+    return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
   mark();
   if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, s)) < 0)
@@ -203,9 +234,11 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
   if (what == Out::Emb) {
     r = launch_gather_emb(ev, K, nK, g, tb, c->acc, c->ncnt, out, c->err, s);
   } else if (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)) {
-    r = launch_predict_tc(ev, K, nK, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
+    r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
+                          c->off + P, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
   } else {
-    r = launch_predict_fp32(ev, K, nK, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
+    r = launch_predict_fp32(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
+                            c->off + P, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
     if (r == -2) return fail(VECKM_EUNSUPPORTED, "FP32 perceptron needs 2D*128 floats of shared memory; D=%d is too large", g.D);
   }
   if (r < 0) return cuda_fail(cudaGetLastError(), "gather launch");
@@ -246,8 +279,8 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   if (cfg->dx < 0 || cfg->dx > 64 || cfg->dy < 0 || cfg->dy > 64)
     return fail(VECKM_EINVAL, "window radii (%d,%d) outside 0..64", cfg->dx, cfg->dy);
   if (cfg->hidden != 128) return fail(VECKM_EINVAL, "hidden=%d; this build supports 128", cfg->hidden);
-  // the pooling walker keeps one window of D/2 float4 units per lane in shared memory
-  if ((size_t)(2 * std::max(cfg->dx, cfg->dy) + 1) * (cfg->D / 2) * 16 > 200 * 1024)
+  // the pooling walker streams three windows of D/2 float4 units per warp through shared memory
+  if ((size_t)3 * (2 * std::max(cfg->dx, cfg->dy) + 2) * (cfg->D / 2) * 16 > 220 * 1024)
     return fail(VECKM_EUNSUPPORTED, "window %dx%d too large for D=%d", 2 * cfg->dx + 1,
                 2 * cfg->dy + 1, cfg->D);
   if (cfg->dt_us <= 0) return fail(VECKM_EINVAL, "dt_us must be positive");
@@ -291,11 +324,21 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   // tables
   const double wx = cfg->dx > 0 ? 1.0 / cfg->dx : 0.0, wy = cfg->dy > 0 ? 1.0 / cfg->dy : 0.0;
   const double wt = 1.0 / (double)cfg->dt_us;
-  c->nhi = (int)((span >> kTLoBits) + 1);
-  std::vector<float> htx = phase_rows(c->X, wx, g.W, 1);
-  std::vector<float> hty = phase_rows(c->Y, wy, g.H, 1);
-  std::vector<float> hlo = phase_rows(c->T, wt, kTLo, 1);
-  std::vector<float> hhi = phase_rows(c->T, wt, c->nhi, kTLo);
+  std::vector<float> htx = phase_rows(c->X, wx, -cfg->dx, (int64_t)g.W + cfg->dx, 1);
+  std::vector<float> hty = phase_rows(c->Y, wy, 0, g.H, 1);
+  std::vector<float> hsx = phase_rows(c->X, wx, 1, 1, 1);
+  std::vector<float> hsy = phase_rows(c->Y, wy, 1, 1, 1);
+  // temporal frequencies in turns per microsecond, reduced to [-1/2, 1/2],
+  // as 64-bit fixed point (the device reduces t * w mod 1 exactly)
+  std::vector<uint2> hwt(D);
+  for (int d = 0; d < D; ++d) {
+    const double w = c->T[d] * wt / (2.0 * 3.14159265358979323846);
+    const double r = w - std::nearbyint(w);
+    const double q = std::ldexp(r, 64);
+    const int64_t qi = q >= 9.2233720368547758e18 ? INT64_MAX : (int64_t)std::llround(q);
+    const uint64_t u = (uint64_t)qi;
+    hwt[d] = make_uint2((uint32_t)(u & 0xffffffffu), (uint32_t)(u >> 32));
+  }
   const int IN = 2 * D;
   c->hW1.assign(cfg->h_W1, cfg->h_W1 + (size_t)c->hidden * IN);
   std::vector<float> hW1t((size_t)IN * c->hidden);
@@ -309,10 +352,11 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   do {                                  \
     if (e == cudaSuccess) e = (expr);   \
   } while (0)
-  VK_TRY(dalloc(&c->tx, (size_t)g.W * g.U));
+  VK_TRY(dalloc(&c->tx, ((size_t)g.W + cfg->dx) * g.U));
+  VK_TRY(dalloc(&c->sx, (size_t)g.U));
+  VK_TRY(dalloc(&c->sy, (size_t)g.U));
   VK_TRY(dalloc(&c->ty, (size_t)g.H * g.U));
-  VK_TRY(dalloc(&c->tt_lo, (size_t)kTLo * g.U));
-  VK_TRY(dalloc(&c->tt_hi, (size_t)c->nhi * g.U));
+  VK_TRY(dalloc(&c->wt, (size_t)D));
   VK_TRY(dalloc(&c->W1, (size_t)c->hidden * IN));
   VK_TRY(dalloc(&c->W1t, (size_t)c->hidden * IN));
   VK_TRY(dalloc(&c->W1h, (size_t)c->hidden * IN));
@@ -324,12 +368,17 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(dalloc(&c->cnt, P));
   VK_TRY(dalloc(&c->cnt_tmp, P));
   VK_TRY(dalloc(&c->ncnt, P));
+  VK_TRY(dalloc(&c->off, P + 1));
+  VK_TRY(dalloc(&c->cur, P));
+  VK_TRY(dalloc(&c->bsum, (size_t)scan_blocks((int64_t)P)));
+  VK_TRY(dalloc(&c->total, 1));
   VK_TRY(dalloc(&c->err, 1));
   VK_TRY(cudaMallocHost(reinterpret_cast<void **>(&c->h_err), sizeof(int)));
   VK_TRY(cudaMemcpy(c->tx, htx.data(), htx.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->ty, hty.data(), hty.size() * 4, cudaMemcpyHostToDevice));
-  VK_TRY(cudaMemcpy(c->tt_lo, hlo.data(), hlo.size() * 4, cudaMemcpyHostToDevice));
-  VK_TRY(cudaMemcpy(c->tt_hi, hhi.data(), hhi.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->sx, hsx.data(), hsx.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->sy, hsy.data(), hsy.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->wt, hwt.data(), hwt.size() * sizeof(uint2), cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1, c->hW1.data(), c->hW1.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1t, hW1t.data(), hW1t.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1h, hW1h.data(), hW1h.size() * 2, cudaMemcpyHostToDevice));

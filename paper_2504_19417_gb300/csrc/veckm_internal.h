@@ -10,10 +10,6 @@ namespace veckm {
 // Bits of the device error word.
 enum : int { ERR_EVENT_RANGE = 1, ERR_INDEX_RANGE = 2, ERR_TIMEOUT = 4 };
 
-// Low level of the split time table: t_rel = 64 a + b.
-constexpr int kTLoBits = 6;
-constexpr int kTLo = 1 << kTLoBits;
-
 // Device view of one slice's events.
 struct Events {
   const int16_t *x, *y;
@@ -31,10 +27,12 @@ struct Geometry {
 };
 
 struct Tables {
-  const float4 *tx;     // [W][U]   exp(i x X/dx), x in [0, W)
-  const float4 *ty;     // [H][U]   exp(i y Y/dy), y in [0, H)
-  const float4 *tt_lo;  // [64][U]  exp(i b T/dt), b in [0, 64)
-  const float4 *tt_hi;  // [NH][U]  exp(i 64 a T/dt), a in [0, NH)
+  const float4 *tx;     // [dx + W][U] exp(i x X/dx), x in [-dx, W), row x + dx
+  const float4 *ty;     // [H][U]      exp(i y Y/dy), y in [0, H)
+  const float4 *sx;     // [U]         exp(i X/dx), one step along x
+  const float4 *sy;     // [U]         exp(i Y/dy), one step along y
+  const uint2 *wt;      // [D]         T_d/(2 pi dt) in turns per microsecond, reduced to
+                        //             [-1/2, 1/2], as 64-bit fixed point (lo, hi words)
 };
 
 struct MLP {
@@ -48,10 +46,21 @@ struct MLP {
   int half_kind;         // 0: BF16, 1: FP16 (for W1h)
 };
 
-// Launchers (kernels.cu).  Each returns the number of kernels it launched
-// (or a negative cudaError_t value on a launch failure).
-int launch_scatter(const Events &ev, const Geometry &g, const Tables &tb, float4 *acc, int *cnt,
-                   int *err, cudaStream_t s);
+// Launchers (kernels.cu, mlp_tc.cu).  Each returns the number of kernels it
+// launched, or a negative value on a launch failure.
+// zero_flow (nullable): flow rows of invalid events are zeroed (sorted prediction).
+int launch_hist(const Events &ev, const Geometry &g, int *cnt, int *err, float *zero_flow,
+                cudaStream_t s);
+int scan_blocks(int64_t P);
+int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur, int *total,
+                cudaStream_t s);
+int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
+                 cudaStream_t s);
+// Clears acc, then sums the *nsorted pixel-sorted records (n bounds it).
+int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
+                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s);
+// Blocks of `threads` threads with `smem` dynamic bytes that fit on one SM.
+int blocks_per_sm(const void *func, int threads, size_t smem);
 // Pooling: row pass acc -> hbuf, column pass hbuf -> acc, window counts.
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
                      cudaStream_t s);
@@ -61,12 +70,17 @@ int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cu
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                       const Tables &tb, const float4 *pooled, const int *ncnt, float *emb,
                       int *err, cudaStream_t s);
-int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
-                        const Tables &tb, const float4 *pooled, const int *ncnt, const MLP &mlp,
-                        float *flow, int *err, cudaStream_t s);
-int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
-                      const Tables &tb, const float4 *pooled, const int *ncnt, const MLP &mlp,
-                      float *flow, int *err, cudaStream_t s);
+// Perceptron launchers: rec/rpix non-null selects the pixel-sorted order
+// (all valid events, *nsorted of them on the device; row i is written to
+// flow[rec[i].y]); otherwise K (or the identity).
+int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                        const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
+                        const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
+                        int *err, cudaStream_t s);
+int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                      const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
+                      const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
+                      int *err, cudaStream_t s);
 
 int num_sms();
 

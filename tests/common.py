@@ -41,6 +41,29 @@ def emb_rel_err(gpu, ref):
     return num / den
 
 
+UNIT_ROUNDOFF = {vk.MLP_BF16: 2.0 ** -8, vk.MLP_FP16: 2.0 ** -11}
+
+
+def half_flow_bound(emb_ref, w, mode):
+    """A-priori bound on |flow_gpu - flow_ref| per output for a first layer whose
+    operands (emb and W1) are rounded to BF16/FP16 (unit roundoff u) and whose
+    products are accumulated in FP32:
+        |dflow_o| <= sum_j |W2_oj| * (2u + u^2 + 1e-5) * sum_c |W1_jc e_c|
+    (each rounded product is W e (1 + d1)(1 + d2); ReLU is 1-Lipschitz; the
+    1e-5 covers FP32 accumulation over at most 256 terms and the FP32 error
+    of the encoder)."""
+    u = UNIT_ROUNDOFF[mode]
+    a = np.abs(emb_ref) @ np.abs(w.W1.astype(np.float64)).T          # [nK, hidden]
+    return (2 * u + u * u + 1e-5) * (a @ np.abs(w.W2.astype(np.float64)).T)  # [nK, 2]
+
+
+def within_half_bound(gpu, ref, emb_ref, w, mode):
+    """max over events and outputs of |dflow| / (bound + 1e-6 (|flow| + 1e-3)); <= 1 passes."""
+    b = half_flow_bound(emb_ref, w, mode)
+    d = np.abs(np.asarray(gpu, np.float64) - ref)
+    return float(np.max(d / (b + 1e-6 * (np.abs(ref) + 1e-3))))
+
+
 def flow_rel_err(gpu, ref, floor_frac=FLOW_FLOOR):
     gpu = np.asarray(gpu, np.float64)
     nr = np.linalg.norm(ref, axis=1)
