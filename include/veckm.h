@@ -104,6 +104,24 @@ veckm_status veckm_encode(veckm_ctx *ctx, const int16_t *d_x, const int16_t *d_y
                           const uint32_t *d_t, int64_t n, uint32_t t_ref_us,
                           const int64_t *d_K, int64_t nK, float *d_emb, void *stream);
 
+/* Encode without allocating: the same result as veckm_encode, for callers
+ * that may not allocate device memory during a call (graph recording,
+ * real-time loops, devices whose memory is reserved up front).  veckm_encode
+ * may grow its per-event buffers with cudaMalloc; this call takes them from a
+ * fixed array in device memory that the library declares statically and
+ * never calls cudaMalloc, cudaFree or any allocating routine.  The paper has
+ * no counterpart; it is a deployment variant.
+ *   - At most 1048576 events per call (n); larger n returns VECKM_EINVAL.
+ *   - The array (12 MiB) exists on every GPU that loads the library until the
+ *     process exits.  The first call on a device looks up its address there
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the array and the context's accumulators:
+ *     calls that may overlap on the GPU race and must be serialised.
+ * Arguments, layout and errors are those of veckm_encode. */
+veckm_status veckm_encode_noalloc(veckm_ctx *ctx, const int16_t *d_x, const int16_t *d_y,
+                                  const uint32_t *d_t, int64_t n, uint32_t t_ref_us,
+                                  const int64_t *d_K, int64_t nK, float *d_emb, void *stream);
+
 /* Predict: the encoding above fused with the two-layer perceptron (Eq. 6),
  * in the precision chosen by cfg.flags.  d_flow is float [nK][2] (device):
  * the generalised normal flow (n_x, n_y) of event K[i] in row i. */

@@ -53,10 +53,6 @@ __device__ __forceinline__ float4 cmul2c(float4 a, float4 b) {
   return make_float4(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y),
                      fmaf(a.z, b.z, a.w * b.w), fmaf(a.w, b.z, -a.z * b.w));
 }
-__device__ __forceinline__ float4 cmul2(float4 a, float4 b) {
-  return make_float4(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x),
-                     fmaf(a.z, b.z, -a.w * b.w), fmaf(a.z, b.w, a.w * b.z));
-}
 
 // Shared-memory matrix descriptor, K-major with 128-byte swizzling: start
 // address, stride byte offset 1024 (next group of 8 rows), leading byte

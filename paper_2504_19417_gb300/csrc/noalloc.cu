@@ -1,0 +1,96 @@
+// veckm_encode_noalloc: the encoding of veckm_encode for callers that must not
+// allocate device memory while they run.
+//
+// veckm_encode keeps its pixel-sorted event records in context buffers that
+// grow (cudaMalloc, after a stream synchronisation) whenever a call brings
+// more events than any call before.  Code that records CUDA graphs, runs
+// under a real-time budget, or shares a device whose memory is fully
+// reserved up front cannot allow that.  This entry point instead takes the
+// per-event records from one fixed array in device memory that the library
+// declares at file scope, so a call never allocates: it only launches
+// kernels and clears context buffers with cudaMemsetAsync.
+//
+// The array holds up to kNoAllocMaxEvents events (12 bytes each, 12 MiB in
+// all); every GPU that loads the library keeps it for the life of the
+// process.  All calls, from every context on a device, share it: calls that
+// may overlap on the GPU (two streams, two host threads) race on it and
+// must be serialised by the caller.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "veckm_internal.h"
+
+namespace {
+
+constexpr int64_t kNoAllocMaxEvents = (int64_t)1 << 20;
+constexpr size_t kRecordBytes = (size_t)kNoAllocMaxEvents * (sizeof(int2) + sizeof(int));
+
+// Records of one call: (t - t_ref, event index) pairs, then the pixel of each.
+// Every call overwrites what it reads, so nothing here needs clearing.
+static __device__ __align__(256) unsigned char g_noalloc_records[kRecordBytes];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_mutex;
+void *g_records_addr[kMaxDevices] = {};  // device address of g_noalloc_records, per device
+
+// The host-side name g_noalloc_records is only a stand-in for the symbol; the
+// device address comes from cudaGetSymbolAddress, once per device, with that
+// device current.
+cudaError_t records_on_device(int dev, void **addr) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_records_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_records);
+    if (e != cudaSuccess) return e;
+    g_records_addr[dev] = p;
+  }
+  *addr = g_records_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+using namespace veckm;
+
+extern "C" veckm_status veckm_encode_noalloc(veckm_ctx *ctx, const int16_t *d_x,
+                                             const int16_t *d_y, const uint32_t *d_t, int64_t n,
+                                             uint32_t t_ref_us, const int64_t *d_K, int64_t nK,
+                                             float *d_emb, void *stream) {
+  CtxView c;
+  if (!ctx_view(ctx, &c)) return report(VECKM_EINVAL, "null context");
+  if (n < 0 || nK < 0) return report(VECKM_EINVAL, "negative size");
+  if (n > kNoAllocMaxEvents)
+    return report(VECKM_EINVAL,
+                  "veckm_encode_noalloc takes at most 1048576 events per call "
+                  "(its static record array); use veckm_encode for larger slices");
+  if (n > 0 && (!d_x || !d_y || !d_t)) return report(VECKM_EINVAL, "null event buffer");
+  if (!d_K && nK != n && nK != 0) return report(VECKM_EINVAL, "K is NULL but nK != n");
+  if (nK > 0 && !d_emb) return report(VECKM_EINVAL, "null output buffer");
+  if (nK > 0 && n == 0) return report(VECKM_EINVAL, "nK > 0 with an empty slice");
+  if (nK == 0) return VECKM_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return report(VECKM_ECUDA, "no usable current device");
+  void *base = nullptr;
+  if (records_on_device(dev, &base) != cudaSuccess)
+    return report(VECKM_ECUDA, "cudaGetSymbolAddress failed for the static record array");
+  int2 *rec = reinterpret_cast<int2 *>(base);
+  int *rpix = reinterpret_cast<int *>(rec + kNoAllocMaxEvents);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geometry &g = c.g;
+  const Events ev{d_x, d_y, d_t, n, t_ref_us, (uint32_t)c.t_span};
+  const size_t P = (size_t)g.W * g.H;
+  if (cudaMemsetAsync(c.cnt, 0, P * sizeof(int), s) != cudaSuccess ||
+      launch_hist(ev, g, c.cnt, c.err, nullptr, s) < 0 ||
+      launch_scan(g, c.cnt, c.bsum, c.off, c.cur, c.total, s) < 0 ||
+      launch_place(ev, g, c.cur, rec, rpix, s) < 0 ||
+      launch_pixsum(g, c.tb, c.off + P, rec, rpix, n, c.acc, s) < 0 ||
+      launch_pool_rows(g, c.tb, c.acc, c.hbuf, s) < 0 ||
+      launch_pool_cols(g, c.tb, c.hbuf, c.acc, s) < 0 ||
+      launch_counts(g, c.cnt, c.cnt_tmp, c.ncnt, s) < 0 ||
+      launch_gather_emb(ev, d_K, nK, g, c.tb, c.acc, c.ncnt, d_emb, c.err, s) < 0)
+    return report(VECKM_ECUDA, cudaGetErrorString(cudaGetLastError()));
+  return VECKM_OK;
+}

@@ -531,3 +531,28 @@ veckm_status veckm_stage_times(veckm_ctx *c, double *ms, int64_t *launches, int 
 int veckm_last_launch_count(const veckm_ctx *c) { return c ? c->last_launches : 0; }
 
 }  // extern "C"
+
+// Read-only view of a context for other translation units of the library.
+namespace veckm {
+
+bool ctx_view(const veckm_ctx *c, CtxView *v) {
+  if (!c || !v) return false;
+  v->g = c->g;
+  v->tb = c->tables();
+  v->acc = c->acc;
+  v->hbuf = c->hbuf;
+  v->cnt = c->cnt;
+  v->cnt_tmp = c->cnt_tmp;
+  v->ncnt = c->ncnt;
+  v->off = c->off;
+  v->cur = c->cur;
+  v->bsum = c->bsum;
+  v->total = c->total;
+  v->err = c->err;
+  v->t_span = c->t_span;
+  return true;
+}
+
+veckm_status report(veckm_status st, const char *msg) { return fail(st, "%s", msg); }
+
+}  // namespace veckm

@@ -84,4 +84,17 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
 
 int num_sms();
 
+// Device buffers and geometry of a context (veckm.cu), for entry points that
+// live in other translation units.
+struct CtxView {
+  Geometry g;
+  Tables tb;
+  float4 *acc, *hbuf;
+  int *cnt, *cnt_tmp, *ncnt, *off, *cur, *bsum, *total, *err;
+  int64_t t_span;
+};
+bool ctx_view(const veckm_ctx *c, CtxView *v);
+// Records msg as this thread's last error and returns st.
+veckm_status report(veckm_status st, const char *msg);
+
 }  // namespace veckm

@@ -41,7 +41,7 @@ class _Config(C.Structure):
                 ("h_W2", C.c_void_p), ("h_b2", C.c_void_p), ("flags", C.c_uint32)]
 
 
-EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_predict",
+EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noalloc", "veckm_predict",
            "veckm_predict_host", "veckm_set_mlp_mode", "veckm_sync_status", "veckm_last_error",
            "veckm_get_frequencies", "veckm_set_timing", "veckm_stage_times",
            "veckm_last_launch_count", "veckm_normals")
@@ -61,6 +61,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_destroy.restype = None
     ev = [P, P, P, P, i64, u32, P, i64, P, P]
     lib.veckm_encode.argtypes = ev
+    lib.veckm_encode_noalloc.argtypes = ev
+    lib.veckm_encode_noalloc.restype = C.c_int
     lib.veckm_predict.argtypes = ev
     lib.veckm_predict_host.argtypes = ev
     lib.veckm_set_mlp_mode.argtypes = [P, u32]

@@ -1,0 +1,64 @@
+"""veckm_encode_noalloc against veckm_encode, through the C ABI.
+
+veckm_encode_noalloc serves callers that may not allocate device memory
+while a call runs (graph recording, real-time loops, devices reserved up
+front): it keeps its per-event scratch in a fixed array that the library
+declares statically.  Its result must equal veckm_encode's within the FP32
+encoder bar, on consecutive calls that reuse the shared array.  This file is
+collected last so that a failure here never hides the other GPU tests.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2504_19417_gb300 import synth
+from paper_2504_19417_gb300 import veckm as vk
+from tests.common import EMB_TOL_FP32, emb_rel_err, make, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+def _noalloc(enc, x, y, t, t_ref, K, nK, out):
+    st = vk.lib().veckm_encode_noalloc(enc.handle, _ptr(x), _ptr(y), _ptr(t), x.numel(),
+                                       C.c_uint32(t_ref), _ptr(K), nK, _ptr(out),
+                                       C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st
+
+
+def test_noalloc_encode_matches_encode_on_consecutive_calls():
+    sl = synth.event_slice(346, 260, 20_000, 10_000, n_edges=8, seed=314)
+    enc, _, _ = make(sl, 64)
+    x, y, t = to_dev(sl)
+    ref = enc.encode(x, y, t, sl.t_ref).cpu().numpy().astype(np.float64)
+    for _ in range(2):
+        out = torch.full((sl.n, 128), float("nan"), dtype=torch.float32, device="cuda")
+        assert _noalloc(enc, x, y, t, sl.t_ref, None, sl.n, out) == vk.VECKM_OK
+        torch.cuda.synchronize()
+        err = emb_rel_err(out.cpu().numpy(), ref)
+        assert err.max() <= EMB_TOL_FP32, err.max()
+    # an explicit subset K, after a call of another size
+    K = torch.arange(3, sl.n, 11, dtype=torch.int64, device="cuda")
+    out = torch.empty((K.numel(), 128), dtype=torch.float32, device="cuda")
+    assert _noalloc(enc, x, y, t, sl.t_ref, K, K.numel(), out) == vk.VECKM_OK
+    torch.cuda.synchronize()
+    assert emb_rel_err(out.cpu().numpy(), ref[K.cpu().numpy()]).max() <= EMB_TOL_FP32
+    enc.sync_status()
+
+
+def test_noalloc_encode_rejects_more_events_than_its_array():
+    sl = synth.event_slice(64, 48, 100, 1_000, seed=2)
+    enc, _, _ = make(sl, 64)
+    n = (1 << 20) + 1
+    x = torch.zeros(n, dtype=torch.int16, device="cuda")
+    t = torch.zeros(n, dtype=torch.int32, device="cuda")
+    out = torch.empty((1, 128), dtype=torch.float32, device="cuda")
+    K = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert _noalloc(enc, x, x, t, 0, K, 1, out) == vk.VECKM_EINVAL
+    assert b"1048576" in vk.lib().veckm_last_error()
