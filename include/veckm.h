@@ -80,7 +80,7 @@ typedef struct {
 } veckm_config;
 
 /* Create a context: validates cfg, draws or copies the frequencies T, X, Y
- * (Algorithm 1, lines 4-6; drawn as SplitMix64 + Box-Muller normals scaled by
+ * (Algorithm 1; drawn as SplitMix64 + Box-Muller normals scaled by
  * sqrt(sigma2)), builds the per-axis phase tables in FP64 and stores them in
  * FP32, uploads the weights and allocates the per-pixel accumulators
  * (2 x W x H x D complex FP32 plus counts) on the current device.
@@ -90,7 +90,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg);
 /* Free everything the context owns.  NULL-safe.  Synchronises the device. */
 void veckm_destroy(veckm_ctx *ctx);
 
-/* Encode: the pooled local event encoding of Algorithm 1 (lines 7-21) for the
+/* Encode: the pooled local event encoding of Algorithm 1 (Eq. 16-17) for the
  * events selected by d_K.
  *   d_x, d_y  int16 pixel coordinates of the n slice events (device)
  *   d_t       uint32 timestamps in microseconds (device); t_ref_us is the slice
@@ -154,9 +154,9 @@ veckm_status veckm_get_frequencies(const veckm_ctx *ctx, double *h_T, double *h_
 
 /* Per-stage timing, measured with CUDA events recorded on the launching
  * stream around each stage.  Stages: 0 clear (memset of the accumulators),
- * 1 scatter (Algorithm 1 lines 7-10), 2 pooling row pass and 3 pooling column
- * pass (the window sums of lines 11-20, Eq. 16), 4 window counts (Eq. 17),
- * 5 gather + normalise (line 21), fused with the perceptron in veckm_predict.
+ * 1 per-pixel accumulation (the first loop of Algorithm 1), 2 pooling row pass
+ * and 3 pooling column pass (the window sums of Eq. 16), 4 window counts
+ * (Eq. 17), 5 gather + normalise, fused with the perceptron in veckm_predict.
  * veckm_stage_times synchronises, writes the elapsed milliseconds summed over
  * every timed call since the last read into ms[0..nstage-1] and the number of
  * timed calls into calls[0..nstage-1] (may be NULL), then resets. */

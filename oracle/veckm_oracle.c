@@ -16,11 +16,11 @@
  *                         exp(i[(t_j-t_k)/dt T + (x_j-x_k)/dx X + (y_j-y_k)/dy Y]).
  *                         This is the adjacency-matrix (O(N^2)) form.
  *   oracle_encode_pooled  Algorithm 1 in its own order: PixelEmbed/PixelCount
- *                         accumulation of the temporal phase (lines 7-10),
+ *                         accumulation of the temporal phase (its first loop),
  *                         then for each requested event the window loop with
  *                         the precomputed spatial phase, the conjugate
  *                         temporal phase and the division by the window
- *                         count (lines 11-21; Eq. 16-17).
+ *                         count (its second loop; Eq. 16-17).
  *   oracle_mlp            The two-layer perceptron of Eq. 6:
  *                         flow = W2 ReLU(W1 [Re emb; Im emb] + b1) + b2.
  *   oracle_kde_query      Lemma 1 of Section 2.2.1: Re((1/D) sum_d emb[d]
@@ -157,7 +157,7 @@ int oracle_encode_pooled(const int16_t *x, const int16_t *y, const uint32_t *t, 
         free(pe_re); free(pe_im); free(pc); free(sx_re); free(sx_im); free(sy_re); free(sy_im);
         return ORC_ENOMEM;
     }
-    /* lines 7-10: accumulate exp(i t_k/dt T) and the count at each event's pixel */
+    /* first loop: accumulate exp(i t_k/dt T) and the count at each event's pixel */
     for (int64_t k = 0; k < n; ++k) {
         const int64_t p = (int64_t)x[k] * H + y[k];
         const double ut = (double)((int64_t)t[k] - (int64_t)t_ref) / dt_us;
@@ -180,7 +180,7 @@ int oracle_encode_pooled(const int16_t *x, const int16_t *y, const uint32_t *t, 
             sy_re[(b + dy) * D + d] = cos(ang);
             sy_im[(b + dy) * D + d] = sin(ang);
         }
-    /* lines 11-21 */
+    /* second loop: window sum with the spatial factors, conjugate phase, 1/count */
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < nK; ++i) {
         const int64_t k = K ? K[i] : i;

@@ -106,29 +106,29 @@ __device__ __forceinline__ void cp_async_wait0() {
 }
 
 // ---------------------------------------------------------------------------
-// 1. counts per pixel; lanes hitting the same pixel add once.
-// In pixel-sorted prediction an invalid event never reaches the perceptron,
-// so its flow row is zeroed here (zero_flow non-null).
+constexpr int kPlaceILP = 4;
+
+// 1. counts per pixel (reductions without return value, kPlaceILP events per
+// thread).  In pixel-sorted prediction an invalid event never reaches the
+// perceptron, so its flow row is zeroed here (zero_flow non-null).
 __global__ void __launch_bounds__(256) k_hist(Events ev, Geometry g, int *__restrict__ cnt,
                                               int *__restrict__ err, float *__restrict__ zero_flow) {
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ev.n;
-       base += stride) {
-    const int64_t k = base + lane;
-    int key = -1;
-    if (k < ev.n) {
-      uint32_t trel;
-      const int x = ev.x[k], y = ev.y[k];
-      if (event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) {
-        key = y * g.W + x;
-      } else {
-        atomicOr(err, ERR_EVENT_RANGE);
-        if (zero_flow) *reinterpret_cast<float2 *>(zero_flow + 2 * k) = make_float2(0.f, 0.f);
+  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < ev.n; k0 += stride * 4) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t k = k0 + e * stride;
+      if (k < ev.n) {
+        uint32_t trel;
+        const int x = ev.x[k], y = ev.y[k];
+        if (event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) {
+          atomicAdd(cnt + y * g.W + x, 1);
+        } else {
+          atomicOr(err, ERR_EVENT_RANGE);
+          if (zero_flow) *reinterpret_cast<float2 *>(zero_flow + 2 * k) = make_float2(0.f, 0.f);
+        }
       }
     }
-    const unsigned grp = __match_any_sync(kFull, key);
-    if (key >= 0 && (__ffs(grp) - 1) == lane) atomicAdd(cnt + key, __popc(grp));
   }
 }
 
@@ -221,30 +221,36 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
   if (b0 < P && b0 + kScanPer >= P) off[P] = run;  // the thread holding the last pixel
 }
 
-// 3. placement: rec[pos] = (t - t_ref, k), pix[pos] = p.
+// 3. placement: rec[pos] = (t - t_ref, k), pix[pos] = p, pos taken from the
+// pixel's cursor.  Each thread places kPlaceILP events whose cursor atomics
+// are in flight together.
+
 __global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__restrict__ cur,
                                                int2 *__restrict__ rec, int *__restrict__ pix) {
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ev.n;
-       base += stride) {
-    const int64_t k = base + lane;
-    int key = -1;
-    uint32_t trel = 0;
-    if (k < ev.n) {
-      const int x = ev.x[k], y = ev.y[k];
-      if (event_ok(x, y, ev.t[k], ev, g.W, g.H, trel)) key = y * g.W + x;
+  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < ev.n;
+       k0 += stride * kPlaceILP) {
+    int key[kPlaceILP], pos[kPlaceILP];
+    uint32_t tr[kPlaceILP];
+#pragma unroll
+    for (int e = 0; e < kPlaceILP; ++e) {
+      const int64_t k = k0 + e * stride;
+      key[e] = -1;
+      tr[e] = 0;
+      if (k < ev.n) {
+        const int x = ev.x[k], y = ev.y[k];
+        if (event_ok(x, y, ev.t[k], ev, g.W, g.H, tr[e])) key[e] = y * g.W + x;
+      }
     }
-    const unsigned grp = __match_any_sync(kFull, key);
-    const int leader = __ffs(grp) - 1;
-    int pos = 0;
-    if (key >= 0 && leader == lane) pos = atomicAdd(cur + key, __popc(grp));
-    pos = __shfl_sync(kFull, pos, leader);
-    if (key >= 0) {
-      pos += __popc(grp & ((1u << lane) - 1u));
-      rec[pos] = make_int2((int)trel, (int)k);
-      pix[pos] = key;
-    }
+#pragma unroll
+    for (int e = 0; e < kPlaceILP; ++e)
+      if (key[e] >= 0) pos[e] = atomicAdd(cur + key[e], 1);
+#pragma unroll
+    for (int e = 0; e < kPlaceILP; ++e)
+      if (key[e] >= 0) {
+        rec[pos[e]] = make_int2((int)tr[e], (int)(k0 + e * stride));
+        pix[pos[e]] = key[e];
+      }
   }
 }
 
@@ -786,7 +792,7 @@ int num_sms() {
 int launch_hist(const Events &ev, const Geometry &g, int *cnt, int *err, float *zero_flow,
                 cudaStream_t s) {
   if (ev.n == 0) return 0;
-  const int grid = (int)std::min<int64_t>((ev.n + 255) / 256, (int64_t)num_sms() * 16);
+  const int grid = (int)std::min<int64_t>((ev.n + 1023) / 1024, (int64_t)num_sms() * 8);
   k_hist<<<grid, 256, 0, s>>>(ev, g, cnt, err, zero_flow);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -806,7 +812,8 @@ int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur
 int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
                  cudaStream_t s) {
   if (ev.n == 0) return 0;
-  const int grid = (int)std::min<int64_t>((ev.n + 255) / 256, (int64_t)num_sms() * 16);
+  const int grid = (int)std::min<int64_t>((ev.n + 256 * kPlaceILP - 1) / (256 * kPlaceILP),
+                                          (int64_t)num_sms() * 8);
   k_place<<<grid, 256, 0, s>>>(ev, g, cur, rec, pix);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

@@ -12,7 +12,7 @@ Each test fixes a property that the paper or plain mathematics determines:
   * Lemma 1: (1/D)<emb, phi(q)> approaches a Gaussian kernel density as D grows;
   * the perceptron on a hand-worked example and its zero-weight closed form;
   * SplitMix64's published outputs and the N(0, 25) frequency law (Alg. 1
-    lines 4-6).
+    frequencies).
 A planted mistake in any one of the oracle's steps (a dropped term, a sign,
 a swapped axis, a wrong normaliser) breaks at least one of these.
 """
