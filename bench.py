@@ -131,7 +131,7 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes(sl, D, nK, touched, touched_K):
+def algorithmic_bytes(sl, D, nK, touched, touched_K, acc16=False):
     """Bytes each stage must move at minimum (one launch), per the model in the
     design notes: complex FP32 = 8 B per channel, counts and offsets 4 B,
     events 8 B (x, y int16 + t uint32), sorted records 12 B (t, index, pixel),
@@ -143,9 +143,9 @@ def algorithmic_bytes(sl, D, nK, touched, touched_K):
         "sort": 8 * N + 12 * N + 16 * P,
         "pixsum": 8 * N + 4 * P + P * pix,
         "pool_rows": 2 * P * pix,
-        "pool_cols": 2 * P * pix,
+        "pool_cols": P * pix + (P * pix // 2 if acc16 else P * pix),
         "counts": 16 * P,
-        "gather": 12 * nK + touched_K * (pix + 4) + 8 * nK,
+        "gather": 12 * nK + touched_K * (pix // 2 if acc16 else pix + 4) + 8 * nK,
     }
 
 
@@ -206,7 +206,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2504_19417_gb300 import synth
     from paper_2504_19417_gb300 import veckm as vk
-    modes = {"bf16": vk.MLP_BF16, "fp16": vk.MLP_FP16, "fp32": vk.MLP_FP32}
+    modes = {"bf16": vk.MLP_BF16, "fp16": vk.MLP_FP16, "fp32": vk.MLP_FP32,
+             "fp16-acc16": vk.MLP_FP16 | vk.ACC_FP16, "bf16-acc16": vk.MLP_BF16 | vk.ACC_FP16}
     mode = modes[args.mode]
     w_def = dict(synth.WORKLOADS[args.workload])
     w_def["seed"] = w_def["seed"] + 100 * rank  # each rank its own independent slice
@@ -270,7 +271,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16": "f32+bf16", "fp16": "f32+f16", "fp32": "f32"}[args.mode],
+        "dtype": {"bf16": "f32+bf16", "fp16": "f32+f16", "fp32": "f32",
+                  "fp16-acc16": "f32+f16", "bf16-acc16": "f32+f16+bf16"}[args.mode],
         "data": "synthetic",
         "config": {"workload": args.workload, "sensor": f"{sl.width}x{sl.height}",
                    "events_per_slice": sl.n, "flows_per_step": nK, "D": D, "window": "21x21",
@@ -288,7 +290,7 @@ def run_ours(args):
     pk = _peaks()
     key = sl.y.astype(np.int64) * sl.width + sl.x
     touched = int(np.unique(key).size)
-    ab = algorithmic_bytes(sl, D, nK, touched, touched)
+    ab = algorithmic_bytes(sl, D, nK, touched, touched, acc16=bool(mode & vk.ACC_FP16))
     kern = {}
     for name in stage_ms:
         n = max(1, int(stage_calls[name]))
@@ -390,7 +392,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--mode", default="bf16",
+                    choices=["bf16", "fp16", "fp32", "fp16-acc16", "bf16-acc16"])
     ap.add_argument("--lean", action="store_true", help="timed device loop only (for profilers)")
     ap.add_argument("--scale", type=float, default=1.0, help="events x scale (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

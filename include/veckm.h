@@ -61,6 +61,11 @@ typedef enum {
 #define VECKM_MLP_FP32 0u        /* perceptron in FP32 on the CUDA cores (the plain form) */
 #define VECKM_MLP_BF16 (1u << 0) /* first layer on tcgen05 tensor cores, BF16 x BF16 -> FP32 */
 #define VECKM_MLP_FP16 (1u << 1) /* first layer on tcgen05 tensor cores, FP16 x FP16 -> FP32 */
+/* Store the pooled grid that veckm_predict gathers from as FP16, divided by
+ * the window count (half the bytes; the conjugate-phase product is formed in
+ * packed half2 arithmetic).  Needs VECKM_MLP_BF16 or VECKM_MLP_FP16;
+ * veckm_encode keeps FP32 throughout. */
+#define VECKM_ACC_FP16 (1u << 2)
 
 typedef struct {
     int32_t width, height; /* sensor W x H in pixels (Algorithm 1 inputs), 1..32767 */
@@ -76,7 +81,7 @@ typedef struct {
     const float *h_b1;     /* [hidden] */
     const float *h_W2;     /* [2][hidden] row-major */
     const float *h_b2;     /* [2] */
-    uint32_t flags;        /* VECKM_MLP_* */
+    uint32_t flags;        /* VECKM_MLP_* | VECKM_ACC_FP16 */
 } veckm_config;
 
 /* Create a context: validates cfg, draws or copies the frequencies T, X, Y
@@ -138,8 +143,9 @@ veckm_status veckm_predict_host(veckm_ctx *ctx, const int16_t *h_x, const int16_
                                 const uint32_t *h_t, int64_t n, uint32_t t_ref_us,
                                 const int64_t *h_K, int64_t nK, float *h_flow, void *stream);
 
-/* Switch the perceptron precision of an existing context (VECKM_MLP_* flags);
- * tables and accumulators are kept.  Synchronous. */
+/* Switch the perceptron precision and pooled-grid storage of an existing
+ * context (VECKM_MLP_* | VECKM_ACC_FP16); tables and accumulators are kept.
+ * Synchronous. */
 veckm_status veckm_set_mlp_mode(veckm_ctx *ctx, uint32_t flags);
 
 /* Synchronise the stream, then read and clear the device error word:
@@ -154,9 +160,9 @@ veckm_status veckm_get_frequencies(const veckm_ctx *ctx, double *h_T, double *h_
 
 /* Per-stage timing, measured with CUDA events recorded on the launching
  * stream around each stage.  Stages: 0 clear (memset of the accumulators),
- * 1 per-pixel accumulation (the first loop of Algorithm 1), 2 pooling row pass
- * and 3 pooling column pass (the window sums of Eq. 16), 4 window counts
- * (Eq. 17), 5 gather + normalise, fused with the perceptron in veckm_predict.
+ * 1 per-pixel accumulation (the first loop of Algorithm 1), 2 pooling row pass,
+ * 3 window counts (Eq. 17), 4 pooling column pass (the window sums of
+ * Eq. 16), 5 gather + normalise, fused with the perceptron in veckm_predict.
  * veckm_stage_times synchronises, writes the elapsed milliseconds summed over
  * every timed call since the last read into ms[0..nstage-1] and the number of
  * timed calls into calls[0..nstage-1] (may be NULL), then resets. */

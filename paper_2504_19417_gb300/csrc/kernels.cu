@@ -39,6 +39,7 @@
 // next), so every window sum adds only values inside that window: there is
 // no running-sum subtraction, whose cancellation next to a dense pixel would
 // destroy the result of a sparse one.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -338,10 +339,15 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
 // same phase, advancing in y from an anchor per output block.
 enum class Pass { Rows, Cols };
 
-template <int DV, Pass P>
+// HALF (column pass only): the output is divided by the pixel's window count
+// n (Eq. 17; 0 where the window is empty) and stored as FP16, unit u of a
+// pixel = 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
+template <int DV, Pass P, bool HALF = false>
 __global__ void __launch_bounds__(64) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
-                                                 int seg, int nseg) {
+                                                 int seg, int nseg,
+                                                 const int *__restrict__ ncnt = nullptr) {
+  static_assert(!HALF || P == Pass::Cols, "FP16 output is written by the column pass");
   constexpr int U = 32 * DV;
   extern __shared__ float4 smem[];
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
@@ -430,6 +436,15 @@ __global__ void __launch_bounds__(64) k_box_pass(const float4 *__restrict__ src,
     }
   };
 
+  // HALF: reciprocal window counts of output block bb, one per lane
+  auto load_inv = [&](int bb) {
+    const int q = lane < L ? lane : 0;
+    const int j = bb * L + q;
+    const int n = j < nout ? __ldg(ncnt + (size_t)(o0 + j) * g.W + line) : 0;
+    return n > 0 ? 1.0f / (float)n : 0.f;
+  };
+  float inv_next = HALF ? load_inv(0) : 0.f;
+
   issue(0);
   issue(1);
   cp_async_wait1();
@@ -447,8 +462,15 @@ __global__ void __launch_bounds__(64) k_box_pass(const float4 *__restrict__ src,
 #pragma unroll
       for (int v = 0; v < DV; ++v) dph[v] = cmul2(fl[v], S[L * U + lane + 32 * v]);
     }
+    float inv_lane = 0.f;  // HALF: 1/n of output j0 + lane (lanes < L), loaded a block ahead
+    if (HALF) {
+      inv_lane = inv_next;
+      if (b + 1 < nb) inv_next = load_inv(b + 1);
+    }
     auto emit = [&](int j, int qs, const float4 *G) {
       const int pos = o0 + j;
+      float inv = 0.f;
+      if (HALF) inv = __shfl_sync(kFull, inv_lane, j - j0);
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
         const int u = lane + 32 * v;
@@ -458,7 +480,15 @@ __global__ void __launch_bounds__(64) k_box_pass(const float4 *__restrict__ src,
           o = cmul2c(o, dph[v]);
           dph[v] = cmul2(dph[v], st[v]);
         }
-        dst[base + (size_t)pos * stride + u] = o;
+        if (HALF) {
+          const __half2 re = __floats2half2_rn(o.x * inv, o.z * inv);
+          const __half2 im = __floats2half2_rn(o.y * inv, o.w * inv);
+          reinterpret_cast<uint2 *>(dst)[base + (size_t)pos * stride + u] =
+              make_uint2(*reinterpret_cast<const uint32_t *>(&re),
+                         *reinterpret_cast<const uint32_t *>(&im));
+        } else {
+          dst[base + (size_t)pos * stride + u] = o;
+        }
       }
     };
     emit(j0, 0, nullptr);  // window == block b
@@ -706,8 +736,9 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-template <int DV, Pass P>
-int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s) {
+template <int DV, Pass P, bool HALF = false>
+int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s,
+             const int *ncnt = nullptr) {
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
   const int L = 2 * r + 1;
   const int len = (P == Pass::Rows) ? g.W : g.H;
@@ -717,10 +748,10 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   const size_t per_warp = (size_t)3 * (L + 1) * 32 * DV * sizeof(float4);
   const int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
   const size_t sm = per_warp * wpb;
-  if (set_smem(k_box_pass<DV, P>, sm) != cudaSuccess) return -1;
+  if (set_smem(k_box_pass<DV, P, HALF>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const int grid = (int)((warps + wpb - 1) / wpb);
-  k_box_pass<DV, P><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg);
+  k_box_pass<DV, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, ncnt);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -831,6 +862,13 @@ int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, flo
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
                      cudaStream_t s) {
   VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols>(g, tb, hbuf, acc, s)));
+}
+
+int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbuf,
+                          const int *ncnt, void *pooled16, cudaStream_t s) {
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, true>(g, tb, hbuf,
+                                                         reinterpret_cast<float4 *>(pooled16), s,
+                                                         ncnt)));
 }
 
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s) {

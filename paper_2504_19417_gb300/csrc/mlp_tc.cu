@@ -107,6 +107,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// d = a * b + c on two FP32 lanes at once (packed FP32x2, one instruction)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const uint64_t *>(&a)), "l"(*reinterpret_cast<const uint64_t *>(&b)),
+        "l"(*reinterpret_cast<const uint64_t *>(&c)));
+  return *reinterpret_cast<const float2 *>(&d);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -125,12 +135,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int DV>
+template <int DV, bool HALF>
 __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
     k_predict_tc(Events ev, const int64_t *__restrict__ K, int64_t nK,
                  const int2 *__restrict__ rec, const int *__restrict__ rpix,
                  const int *__restrict__ nsorted, Geometry g, Tables tb,
-                 const float4 *__restrict__ pooled, const int *__restrict__ ncnt, MLP mlp,
+                 const void *__restrict__ pooled_v, const int *__restrict__ ncnt, MLP mlp,
                  float *__restrict__ flow, int *err) {
   constexpr int U = 32 * DV;
   constexpr int IN = 4 * U;  // 2D, the MMA K extent
@@ -199,8 +209,40 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       wf[v][0] = __ldg(tb.wt + 2 * (lane + 32 * v));
       wf[v][1] = __ldg(tb.wt + 2 * (lane + 32 * v) + 1);
     }
-    // per-lane column offsets inside a row: Re at k = 2u, Im at k = D + 2u
-    // (both in chunk (u / 4) of their K-block, byte (u % 4) * 4)
+    // row metadata of tile t for this lane: pixel (-1 if none/invalid), t - t_ref, output row
+    auto meta = [&](int64_t t, int &pix, uint32_t &trel, int64_t &outk) {
+      const int64_t i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
+      pix = -1;
+      trel = 0;
+      outk = -1;
+      if (i >= ns) return;
+      if (rec) {
+        const int2 r = __ldg(rec + i);
+        pix = __ldg(rpix + i);
+        trel = (uint32_t)r.x;
+        outk = r.y;
+        return;
+      }
+      int64_t k = i;
+      if (K) {
+        k = K[i];
+        if (k < 0 || k >= ev.n) {
+          if (lane < kRowsPerWarp) atomicOr(err, ERR_INDEX_RANGE);
+          outk = i | kInvalidRow;  // an invalid index's row gets zeros
+          return;
+        }
+      }
+      const int x = ev.x[k], y = ev.y[k];
+      const uint32_t tt = ev.t[k];
+      trel = tt - ev.t_ref;
+      if (x >= 0 && x < g.W && y >= 0 && y < g.H && tt >= ev.t_ref && trel <= ev.t_span)
+        pix = y * g.W + x;
+      outk = pix >= 0 ? i : (i | kInvalidRow);  // an invalid event's row gets zeros
+    };
+    int m_pix;
+    uint32_t m_trel;
+    int64_t m_outk;
+    if (nlocal > 0) meta(blockIdx.x, m_pix, m_trel, m_outk);
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
       const int64_t tile = blockIdx.x + (int64_t)li * gridDim.x;
@@ -213,61 +255,50 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
         const int64_t i = nt * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
         if (i < ns) {
           const int p = __ldg(rpix + i);
-          const char *row = reinterpret_cast<const char *>(pooled + (size_t)p * U);
+          constexpr int kRowBytes = (HALF ? 8 : 16) * U;  // pooled bytes per pixel
+          constexpr int kHalfLines = kRowBytes / 256;      // 128-byte lines per half row
+          const char *row = reinterpret_cast<const char *>(pooled_v) + (size_t)p * kRowBytes;
 #pragma unroll
-          for (int l = 0; l < 2 * DV; ++l)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ((lane >> 4) * 2 * DV + l) * 128));
+          for (int l = 0; l < kHalfLines; ++l)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ((lane >> 4) * kHalfLines + l) * 128));
         }
       }
-      // lane j < 16 holds the metadata of row pw*16 + j
-      const int64_t i = tile * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
-      int pix = -1;
-      uint32_t trel = 0;
-      int64_t outk = -1;
-      if (i < ns) {
-        if (rec) {
-          const int2 r = __ldg(rec + i);
-          pix = __ldg(rpix + i);
-          trel = (uint32_t)r.x;
-          outk = r.y;
-        } else {
-          int64_t k = i;
-          bool kok = true;
-          if (K) {
-            k = K[i];
-            if (k < 0 || k >= ev.n) {
-              if (lane < kRowsPerWarp) atomicOr(err, ERR_INDEX_RANGE);
-              kok = false;
-            }
-          }
-          if (kok) {
-            const int x = ev.x[k], y = ev.y[k];
-            const uint32_t t = ev.t[k];
-            trel = t - ev.t_ref;
-            if (x >= 0 && x < g.W && y >= 0 && y < g.H && t >= ev.t_ref && trel <= ev.t_span)
-              pix = y * g.W + x;
-          }
-          outk = pix >= 0 ? i : (i | kInvalidRow);  // an invalid event's row gets zeros
-        }
-      }
+      // lane j < 16 holds the metadata of row pw*16 + j (loaded one tile ahead)
+      const int pix = m_pix;
+      const uint32_t trel = m_trel;
+      const int64_t outk = m_outk;
+      if (li + 1 < nlocal) meta(tile + gridDim.x, m_pix, m_trel, m_outk);
       if (lane < kRowsPerWarp) {
         sK[b * kM + pw * kRowsPerWarp + lane] = outk;
-        sInv[b * kM + pw * kRowsPerWarp + lane] = pix >= 0 ? 1.0f / (float)__ldg(ncnt + pix) : 0.f;
+        sInv[b * kM + pw * kRowsPerWarp + lane] =
+            pix < 0 ? 0.f : (HALF ? 1.f : 1.0f / (float)__ldg(ncnt + pix));
       }
       uint8_t *A = sA + b * TILE_BYTES;
-      constexpr int kB = 4 / DV;
+      // rows whose loads are issued together: 8 x 8 bytes per lane on the FP16
+      // grid, 4 x 16 bytes on the FP32 grid
+      constexpr int kB = HALF ? 8 / DV : 4 / DV;
 #pragma unroll
       for (int j0 = 0; j0 < kRowsPerWarp; j0 += kB) {
+        // FP32 grid: float4 (re 2u, im 2u, re 2u+1, im 2u+1) per unit;
+        // FP16 grid: uint2 (half2 re pair, half2 im pair), already divided by n
         float4 pv[kB][DV];
+        uint2 qv[kB][DV];
         uint32_t tjs[kB];
 #pragma unroll
         for (int r = 0; r < kB; ++r) {
           const int pj = __shfl_sync(kFull, pix, j0 + r);
           tjs[r] = __shfl_sync(kFull, trel, j0 + r);
 #pragma unroll
-          for (int v = 0; v < DV; ++v)
-            pv[r][v] = pj >= 0 ? __ldg(pooled + (size_t)pj * U + lane + 32 * v)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int v = 0; v < DV; ++v) {
+            if constexpr (HALF)
+              qv[r][v] = pj >= 0 ? __ldg(reinterpret_cast<const uint2 *>(pooled_v) +
+                                         (size_t)pj * U + lane + 32 * v)
+                                 : make_uint2(0u, 0u);
+            else
+              pv[r][v] = pj >= 0 ? __ldg(reinterpret_cast<const float4 *>(pooled_v) +
+                                         (size_t)pj * U + lane + 32 * v)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
 #pragma unroll
         for (int r = 0; r < kB; ++r) {
@@ -276,14 +307,36 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
 #pragma unroll
           for (int v = 0; v < DV; ++v) {
             const int u = lane + 32 * v;
-            const float4 e = cmul2c(pv[r][v], time_phase2(tjs[r], wf[v][0], wf[v][1]));
             const uint32_t kr = 2 * u, ki = D + 2 * u;
             const uint32_t cr = (kr >> 6) * (kM * 128) + rowoff +
                                 ((((kr >> 3) & 7) ^ (m & 7)) << 4) + (kr & 7) * 2;
             const uint32_t ci = (ki >> 6) * (kM * 128) + rowoff +
                                 ((((ki >> 3) & 7) ^ (m & 7)) << 4) + (ki & 7) * 2;
-            *reinterpret_cast<uint32_t *>(A + cr) = pack2(e.x, e.z, fp16);
-            *reinterpret_cast<uint32_t *>(A + ci) = pack2(e.y, e.w, fp16);
+            const float4 ph = time_phase2(tjs[r], wf[v][0], wf[v][1]);  // (c0, s0, c1, s1)
+            uint32_t wre, wim;
+            if constexpr (HALF) {
+              // packed half2: Re = PR C + PI S, Im = PI C - PR S (both channels at once)
+              const __half2 PR = *reinterpret_cast<const __half2 *>(&qv[r][v].x);
+              const __half2 PI = *reinterpret_cast<const __half2 *>(&qv[r][v].y);
+              const __half2 C = __floats2half2_rn(ph.x, ph.z);
+              const __half2 S = __floats2half2_rn(ph.y, ph.w);
+              const __half2 ER = __hfma2(PR, C, __hmul2(PI, S));
+              const __half2 EI = __hfma2(PI, C, __hneg2(__hmul2(PR, S)));
+              if (fp16) {
+                wre = *reinterpret_cast<const uint32_t *>(&ER);
+                wim = *reinterpret_cast<const uint32_t *>(&EI);
+              } else {
+                const float2 fr = __half22float2(ER), fi = __half22float2(EI);
+                wre = pack2(fr.x, fr.y, 0);
+                wim = pack2(fi.x, fi.y, 0);
+              }
+            } else {
+              const float4 e = cmul2c(pv[r][v], ph);
+              wre = pack2(e.x, e.z, fp16);
+              wim = pack2(e.y, e.w, fp16);
+            }
+            *reinterpret_cast<uint32_t *>(A + cr) = wre;
+            *reinterpret_cast<uint32_t *>(A + ci) = wim;
           }
         }
       }
@@ -342,7 +395,9 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float inv = sInv[b * kM + row];
       const int64_t k = sK[b * kM + row];
-      float o0 = 0.f, o1 = 0.f;
+      // packed FP32x2 arithmetic: even and odd columns in the two halves
+      float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
+      const float2 inv2 = make_float2(inv, inv);
       const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kN);
 #pragma unroll
       for (int c0 = 0; c0 < kN; c0 += 16) {
@@ -353,12 +408,14 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
           const float4 bb = *reinterpret_cast<const float4 *>(sB1 + c0 + j);
           const float4 w0 = *reinterpret_cast<const float4 *>(sW2 + c0 + j);
           const float4 w1 = *reinterpret_cast<const float4 *>(sW2 + kN + c0 + j);
-          const float a0 = fmaxf(fmaf(h[j], inv, bb.x), 0.f);
-          const float a1 = fmaxf(fmaf(h[j + 1], inv, bb.y), 0.f);
-          const float a2 = fmaxf(fmaf(h[j + 2], inv, bb.z), 0.f);
-          const float a3 = fmaxf(fmaf(h[j + 3], inv, bb.w), 0.f);
-          o0 = fmaf(a3, w0.w, fmaf(a2, w0.z, fmaf(a1, w0.y, fmaf(a0, w0.x, o0))));
-          o1 = fmaf(a3, w1.w, fmaf(a2, w1.z, fmaf(a1, w1.y, fmaf(a0, w1.x, o1))));
+          float2 a01 = ffma2(make_float2(h[j], h[j + 1]), inv2, make_float2(bb.x, bb.y));
+          float2 a23 = ffma2(make_float2(h[j + 2], h[j + 3]), inv2, make_float2(bb.z, bb.w));
+          a01.x = fmaxf(a01.x, 0.f); a01.y = fmaxf(a01.y, 0.f);
+          a23.x = fmaxf(a23.x, 0.f); a23.y = fmaxf(a23.y, 0.f);
+          o0 = ffma2(a01, make_float2(w0.x, w0.y), o0);
+          o0 = ffma2(a23, make_float2(w0.z, w0.w), o0);
+          o1 = ffma2(a01, make_float2(w1.x, w1.y), o1);
+          o1 = ffma2(a23, make_float2(w1.z, w1.w), o1);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -367,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       if (k >= 0) {
         const bool valid = !(k & kInvalidRow);
         *reinterpret_cast<float2 *>(flow + 2 * (k & ~kInvalidRow)) =
-            valid ? make_float2(o0 + b20, o1 + b21) : make_float2(0.f, 0.f);
+            valid ? make_float2(o0.x + o0.y + b20, o1.x + o1.y + b21) : make_float2(0.f, 0.f);
       }
     }
   }
@@ -385,26 +442,26 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
   }
 }
 
-template <int DV>
+template <int DV, bool HALF>
 int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                     const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
-                    const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
+                    const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
                     cudaStream_t s) {
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
   const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (3 * kN + 2 * kM) +
                     sizeof(int64_t) * 2 * kM + 8 * 6 + 16 + 1024;  // + SW128 alignment slack
-  if (cudaFuncSetAttribute(k_predict_tc<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess ||
-      cudaFuncSetAttribute(k_predict_tc<DV>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  auto kern = k_predict_tc<DV, HALF>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return -1;
-  const int per_sm = std::min(blocks_per_sm((const void *)k_predict_tc<DV>, kThreads, sm),
-                              512 / kTmemCols);
+  const int per_sm = std::min(blocks_per_sm((const void *)kern, kThreads, sm), 512 / kTmemCols);
   const int64_t tiles = (nK + kM - 1) / kM;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm);
-  k_predict_tc<DV><<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt,
-                                              mlp, flow, err);
+  kern<<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
+                                  err);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -412,13 +469,16 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
 
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
-                      const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
+                      const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
                       int *err, cudaStream_t s) {
+  const bool h = mlp.pooled_half != 0;
   switch (g.U / 32) {
     case 1:
-      return predict_tc_impl<1>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
+      return h ? predict_tc_impl<1, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s)
+               : predict_tc_impl<1, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
     case 2:
-      return predict_tc_impl<2>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
+      return h ? predict_tc_impl<2, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s)
+               : predict_tc_impl<2, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
     default:
       return -1;  // 2D > 256 does not fit the operand tiles in shared memory
   }

@@ -42,7 +42,7 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
-constexpr int kStages = 6;  // sort, pixel sums, pool rows, pool cols, counts, gather
+constexpr int kStages = 6;  // sort, pixel sums, pool rows, counts, pool cols, gather
 
 }  // namespace
 
@@ -81,7 +81,7 @@ struct veckm_ctx {
 
   Tables tables() const { return Tables{tx, ty, sx, sy, wt}; }
   MLP mlp() const {
-    return MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0};
+    return MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0};
   }
 };
 
@@ -223,19 +223,26 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
     return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   mark();
-  if ((r = launch_pool_cols(g, tb, c->hbuf, c->acc, s)) < 0)
-    return cuda_fail(cudaGetLastError(), "pooling (columns) launch");
-  launches += r;
-  mark();
   if ((r = launch_counts(g, c->cnt, c->cnt_tmp, c->ncnt, s)) < 0)
     return cuda_fail(cudaGetLastError(), "window count launch");
+  launches += r;
+  mark();
+  // FP16 storage of the normalised pooled grid serves the tensor-core head only
+  const bool half_grid = what == Out::Flow && (c->flags & VECKM_ACC_FP16);
+  if (half_grid)
+    r = launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, s);
+  else
+    r = launch_pool_cols(g, tb, c->hbuf, c->acc, s);
+  if (r < 0) return cuda_fail(cudaGetLastError(), "pooling (columns) launch");
   launches += r;
   mark();
   if (what == Out::Emb) {
     r = launch_gather_emb(ev, K, nK, g, tb, c->acc, c->ncnt, out, c->err, s);
   } else if (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)) {
+    MLP m = c->mlp();
+    m.pooled_half = half_grid ? 1 : 0;
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
-                          c->off + P, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
+                          c->off + P, g, tb, c->acc, c->ncnt, m, out, c->err, s);
   } else {
     r = launch_predict_fp32(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
                             c->off + P, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
@@ -289,7 +296,9 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   if (!cfg->h_W1 || !cfg->h_b1 || !cfg->h_W2 || !cfg->h_b2)
     return fail(VECKM_EINVAL, "perceptron weights are required");
   const uint32_t known = VECKM_MLP_BF16 | VECKM_MLP_FP16;
-  if ((cfg->flags & ~known) || ((cfg->flags & VECKM_MLP_BF16) && (cfg->flags & VECKM_MLP_FP16)))
+  if ((cfg->flags & ~(known | VECKM_ACC_FP16)) ||
+      ((cfg->flags & VECKM_MLP_BF16) && (cfg->flags & VECKM_MLP_FP16)) ||
+      ((cfg->flags & VECKM_ACC_FP16) && !(cfg->flags & known)))
     return fail(VECKM_EINVAL, "bad flags 0x%x", cfg->flags);
   if ((cfg->flags & known) && cfg->D > 128)
     return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
@@ -406,7 +415,8 @@ void veckm_destroy(veckm_ctx *c) {
 veckm_status veckm_set_mlp_mode(veckm_ctx *c, uint32_t flags) {
   if (!c) return fail(VECKM_EINVAL, "null context");
   const uint32_t known = VECKM_MLP_BF16 | VECKM_MLP_FP16;
-  if ((flags & ~known) || ((flags & VECKM_MLP_BF16) && (flags & VECKM_MLP_FP16)))
+  if ((flags & ~(known | VECKM_ACC_FP16)) || ((flags & VECKM_MLP_BF16) && (flags & VECKM_MLP_FP16)) ||
+      ((flags & VECKM_ACC_FP16) && !(flags & known)))
     return fail(VECKM_EINVAL, "bad flags 0x%x", flags);
   if ((flags & known) && c->g.D > 128)
     return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");

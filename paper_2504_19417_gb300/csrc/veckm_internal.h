@@ -44,6 +44,7 @@ struct MLP {
   const uint16_t *W1h;   // [hidden][2D] BF16 or FP16 bits, core-matrix order for tcgen05
   int hidden;
   int half_kind;         // 0: BF16, 1: FP16 (for W1h)
+  int pooled_half;       // 1: the pooled grid is FP16 and already divided by the counts
 };
 
 // Launchers (kernels.cu, mlp_tc.cu).  Each returns the number of kernels it
@@ -67,6 +68,10 @@ int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, flo
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
                      cudaStream_t s);
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s);
+// Column pass writing the pooled grid divided by the window counts as FP16:
+// per pixel D/2 units of 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
+int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbuf,
+                          const int *ncnt, void *pooled16, cudaStream_t s);
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                       const Tables &tb, const float4 *pooled, const int *ncnt, float *emb,
                       int *err, cudaStream_t s);
@@ -77,9 +82,10 @@ int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const in
                         const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                         const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
                         int *err, cudaStream_t s);
+// pooled: float4 FP32 grid, or (mlp.pooled_half) the FP16 grid divided by the counts
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
-                      const float4 *pooled, const int *ncnt, const MLP &mlp, float *flow,
+                      const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
                       int *err, cudaStream_t s);
 
 int num_sms();

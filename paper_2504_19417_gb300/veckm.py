@@ -20,7 +20,8 @@ from . import build as _build
 VECKM_OK, VECKM_EINVAL, VECKM_ENOMEM, VECKM_ECUDA = 0, -1, -2, -3
 VECKM_ERANGE, VECKM_ETIMEOUT, VECKM_EBUSY, VECKM_EUNSUPPORTED = -4, -5, -6, -7
 MLP_FP32, MLP_BF16, MLP_FP16 = 0, 1, 2
-STAGES = ("sort", "pixsum", "pool_rows", "pool_cols", "counts", "gather")
+ACC_FP16 = 4  # or-ed with MLP_BF16 / MLP_FP16: FP16 storage of the normalised pooled grid
+STAGES = ("sort", "pixsum", "pool_rows", "counts", "pool_cols", "gather")
 
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ERANGE", -5: "ETIMEOUT",
            -6: "EBUSY", -7: "EUNSUPPORTED"}

@@ -52,7 +52,7 @@ def _cfg(**kw):
 @pytest.mark.parametrize("bad", [dict(width=0), dict(height=40000), dict(D=96), dict(D=32),
                                  dict(dx=-1), dict(dy=65), dict(hidden=64), dict(dt_us=0),
                                  dict(flags=3), dict(flags=8), dict(t_span_us=1 << 33),
-                                 dict(D=256, flags=1)])
+                                 dict(D=256, flags=1), dict(flags=4)])
 def test_create_rejects_bad_config_on_host(bad):
     c, keep = _cfg(**bad)
     h = C.c_void_p()

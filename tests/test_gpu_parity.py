@@ -83,7 +83,11 @@ def test_subset_K_with_repeats_equals_rows_of_full():
     assert np.array_equal(sub[2], sub[3]) and np.array_equal(sub[5], sub[7])
 
 
-@pytest.mark.parametrize("mode", [vk.MLP_FP32, vk.MLP_FP16, vk.MLP_BF16])
+MODES = [vk.MLP_FP32, vk.MLP_FP16, vk.MLP_BF16, vk.MLP_FP16 | vk.ACC_FP16,
+         vk.MLP_BF16 | vk.ACC_FP16]
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("W,H,n,D", [(346, 260, 20_000, 64), (150, 100, 6_000, 128),
                                      (90, 70, 333, 64)])
 def test_predict_matches_oracle(mode, W, H, n, D):
@@ -100,7 +104,7 @@ def test_switching_precision_keeps_encoder_state():
     enc, TXY, w = make(sl, 64, mode=vk.MLP_FP32)
     x, y, t = to_dev(sl)
     emb_ref = _oracle_emb(sl, 64, 10, 10, 16_000, TXY)
-    for mode in (vk.MLP_BF16, vk.MLP_FP16, vk.MLP_FP32):
+    for mode in (vk.MLP_BF16, vk.MLP_FP16 | vk.ACC_FP16, vk.MLP_FP16, vk.MLP_FP32):
         enc.set_mlp_mode(mode)
         flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
         _check_flow(flow, emb_ref, w, mode)
@@ -177,7 +181,7 @@ def test_out_of_range_event_reports_erange_and_skips_it():
     # predictions: pixel-sorted (all events) and indexed (explicit K) paths
     w = synth.mlp_weights(64, 128, 3)
     fref = oracle.mlp(ref, w.W1, w.b1, w.W2, w.b2)
-    for mode in (vk.MLP_FP32, vk.MLP_BF16):
+    for mode in (vk.MLP_FP32, vk.MLP_BF16, vk.MLP_FP16 | vk.ACC_FP16):
         enc.set_mlp_mode(mode)
         for Kd in (None, torch.arange(sl.n, dtype=torch.int64, device="cuda")):
             f = enc.predict(xd, yd, td, sl.t_ref, K=Kd).cpu().numpy()
@@ -196,7 +200,7 @@ def test_out_of_range_event_reports_erange_and_skips_it():
 def test_index_out_of_range_reports_erange():
     sl = synth.event_slice(60, 50, 500, 10_000, seed=4)
     x, y, t = to_dev(sl)
-    for mode in (vk.MLP_FP32, vk.MLP_BF16):
+    for mode in (vk.MLP_FP32, vk.MLP_BF16, vk.MLP_BF16 | vk.ACC_FP16):
         enc, _, _ = make(sl, 64, mode=mode)
         K = torch.tensor([0, 500, -1, 7], dtype=torch.int64, device="cuda")
         f = enc.predict(x, y, t, sl.t_ref, K=K).cpu().numpy()
@@ -239,7 +243,7 @@ def test_stage_timing_records_every_call():
     assert enc.last_launch_count() >= 4
 
 
-@pytest.mark.parametrize("mode", [vk.MLP_BF16, vk.MLP_FP32])
+@pytest.mark.parametrize("mode", [vk.MLP_BF16, vk.MLP_FP32, vk.MLP_FP16 | vk.ACC_FP16])
 def test_full_size_640x480_sampled(mode):
     """The 640x480, 2M-event workload in the launch configuration the benchmark
     times; the oracle computes a sample of the outputs one by one."""
