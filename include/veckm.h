@@ -46,6 +46,11 @@ extern "C" {
 
 typedef struct veckm_ctx veckm_ctx;
 
+/* Largest n (events of a slice) and nK (requested flows) of one call; larger
+ * sizes return VECKM_EINVAL.  Events are indexed with 32-bit integers on the
+ * device. */
+#define VECKM_MAX_EVENTS ((int64_t)1 << 30)
+
 typedef enum {
     VECKM_OK = 0,
     VECKM_EINVAL = -1,      /* bad argument or configuration */

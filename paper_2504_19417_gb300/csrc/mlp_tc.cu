@@ -1,6 +1,7 @@
 // Perceptron on the 5th-generation tensor cores, fused with the gather.
 //
-// Warp-specialised pipeline, one CTA per SM pair of 128-event tiles in flight:
+// Warp-specialised pipeline, two CTAs per SM, each with two 128-event tiles
+// in flight:
 //   - 8 producer warps gather the rows of a tile, P[p] * conj(exp(i t T/dt))
 //     (the pooled value at the event's pixel times the conjugate temporal
 //     phase, Eq. 16), straight into shared memory as BF16 (or FP16) in the
@@ -8,17 +9,21 @@
 //     split into K-blocks of 64 columns; in K-block kb, row m occupies the
 //     128 bytes at kb * (128 rows * 128 B) + (m / 8) * 1024 + (m % 8) * 128,
 //     and its 16-byte chunk c sits at chunk position c XOR (m % 8), so a warp
-//     writing one row covers 32 distinct banks.  W1 is stored the same way.
-//   - 1 MMA warp issues 2D/16 MMAs of shape 128 x 128 x 16 per tile into one
-//     of two FP32 accumulators in tensor memory (2 x 128 columns) and commits
-//     them to an mbarrier.
-//   - 4 epilogue warps read the accumulator back with tcgen05.ld (warp w owns
-//     TMEM lanes 32w..32w+31, one event row per thread), apply the window
-//     count normalisation and b1 in one FMA (the first layer is linear, so
-//     W1 (x / n) = (W1 x) / n), ReLU, and contract with the 2 x 128 second
+//     writing one row covers 32 distinct banks.  The K axis is ordered per
+//     unit u as Re(2u), Re(2u+1), Im(2u), Im(2u+1) (one 8-byte store per lane
+//     and row); W1 is stored the same way with its columns permuted to match.
+//     Each warp keeps one batch of pooled-row loads in flight while it
+//     computes the previous batch, across tile boundaries.
+//   - 4 epilogue warps; the first also issues the tile's 2D/16 MMAs of shape
+//     128 x 128 x 16 into one of two FP32 accumulators in tensor memory
+//     (2 x 128 columns) and commits them to an mbarrier.  The epilogue reads
+//     the accumulator back with tcgen05.ld (warp w owns TMEM lanes
+//     32w..32w+31, one event row per thread), applies the window count
+//     normalisation and b1 in one FMA (the first layer is linear, so
+//     W1 (x / n) = (W1 x) / n), ReLU, and contracts with the 2 x 128 second
 //     layer on the CUDA cores.
 // Shared tiles and accumulators are double buffered; the hand-offs are
-// mbarriers (full: producers -> MMA and epilogue; mma_done: MMA -> epilogue;
+// mbarriers (full: producers -> epilogue/MMA; mma_done: MMA -> epilogue;
 // tmem_empty: epilogue -> MMA and producers).  No waiter can fall two phases
 // behind a barrier (each role's next use of a buffer waits for the other
 // roles' previous use), so parity waits are unambiguous.  Every wait is
@@ -33,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "phase.cuh"
 #include "veckm_internal.h"
@@ -41,16 +47,18 @@ namespace veckm {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kM = 128;  // events per tile (MMA M)
 constexpr int kN = 128;  // hidden units (MMA N)
 constexpr int kProdWarps = 8;
 constexpr int kEpiWarps = 4;
-constexpr int kMmaWarp = kEpiWarps + kProdWarps;  // warp index of the MMA issuer
-constexpr int kThreads = 32 * (kMmaWarp + 1);
+constexpr int kMmaWarp = 0;  // epilogue warp 0 also issues the MMAs
+constexpr int kThreads = 32 * (kEpiWarps + kProdWarps);
 constexpr int kRowsPerWarp = kM / kProdWarps;
 constexpr int kTmemCols = 2 * kN;  // two accumulators
-constexpr int64_t kInvalidRow = (int64_t)1 << 62;  // output row whose event was invalid
+// Output row codes (event counts are below 2^30): k >= 0 writes the flow of
+// row k; -1 writes nothing; k <= -2 writes zeros to row -2 - k (an invalid
+// event or index).
+__device__ __forceinline__ int invalid_row(int i) { return -2 - i; }
 constexpr long long kWaitLimitCycles = 4000000000LL;  // ~2 s at 2 GHz, then give up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -152,13 +160,13 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
   float *sB1 = reinterpret_cast<float *>(sB + TILE_BYTES);    // [128]
   float *sW2 = sB1 + kN;                                       // [2][128]
   float *sInv = sW2 + 2 * kN;                                  // [2][128] 1 / window count
-  int64_t *sK = reinterpret_cast<int64_t *>(sInv + 2 * kM);    // [2][128] output rows
+  int *sK = reinterpret_cast<int *>(sInv + 2 * kM);            // [2][128] output row codes
   uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 2 * kM);  // full[2], done[2], empty[2]
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 6);
+  int2 *sMeta = reinterpret_cast<int2 *>(bars + 6);             // [8 warps][2][16]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sMeta + kProdWarps * 2 * kRowsPerWarp);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fp16 = mlp.half_kind;
-  const int D = g.D;
 
   {  // W1 (already in SW128 order), b1, W2
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
@@ -193,15 +201,19 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const int64_t ns = rec ? (int64_t)*nsorted : nK;
-  const int64_t ntiles_all = (nK + kM - 1) / kM;
-  const int nlocal = blockIdx.x < ntiles_all
-                         ? (int)((ntiles_all - 1 - blockIdx.x) / gridDim.x + 1)
+  const int ns = rec ? *nsorted : (int)nK;
+  const int ntiles_all = (int)((nK + kM - 1) / kM);
+  const int nlocal = (int)blockIdx.x < ntiles_all
+                         ? (ntiles_all - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
                          : 0;
   bool ok = true;
 
-  if (warp >= kEpiWarps && warp < kMmaWarp) {
+  if (warp >= kEpiWarps) {
     // ------------------------------------------------------------ producers
+    // Warp pw fills rows pw*16 .. pw*16+15 of every tile.  Lane l computes
+    // unit u = l + 32 v (channels 2u, 2u+1) of a row and stores its four
+    // halves, Re(2u) Re(2u+1) Im(2u) Im(2u+1), as one 8-byte group at K
+    // positions 4u..4u+3 (W1's columns are permuted to match on the host).
     const int pw = warp - kEpiWarps;
     uint2 wf[DV][2];  // fixed-point frequencies of this lane's channels
 #pragma unroll
@@ -209,11 +221,30 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       wf[v][0] = __ldg(tb.wt + 2 * (lane + 32 * v));
       wf[v][1] = __ldg(tb.wt + 2 * (lane + 32 * v) + 1);
     }
-    // row metadata of tile t for this lane: pixel (-1 if none/invalid), t - t_ref, output row
-    auto meta = [&](int64_t t, int &pix, uint32_t &trel, int64_t &outk) {
-      const int64_t i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
-      pix = -1;
+    // Byte offset of that group for row pw*16 + j: K-block u / 16 (bits 14+),
+    // row group (bits 10+), row j % 8 (bits 7-9), 16-byte chunk (u / 2) % 8
+    // XOR j % 8 (bits 4-6), half of the chunk u % 2 (bit 3).  For j % 8 == 0
+    // that is lo[v]; for j % 8 == r it is lo[v] ^ (r * 0x90) (r into bits 7-9
+    // and XOR-ed into bits 4-6), and adding a 1024-aligned tile base commutes
+    // with that XOR.
+    uint32_t lo[DV];
+#pragma unroll
+    for (int v = 0; v < DV; ++v) {
+      const uint32_t u = lane + 32 * v;
+      lo[v] = (u >> 4) * (kM * 128) + (uint32_t)pw * 2048 + (((u >> 1) & 7) << 4) + (u & 1) * 8;
+    }
+    // Row metadata of tile t for lane j < 16 (row pw*16 + j): the pixel whose
+    // pooled vector is read, t - t_ref, 1 for a valid event (0 otherwise; the
+    // FP32-grid path later replaces it by 1/n) and the output row (-1: none;
+    // invalid_row(i): an invalid event whose flow is written as zeros).  Rows
+    // past the end and invalid events read pixel 0: the MMA keeps rows apart
+    // and their results are discarded.  Every load here is consumed a tile
+    // later, so the warp never waits on it.
+    auto meta = [&](int t, int &pix, uint32_t &trel, float &inv, int &outk) {
+      const int i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
+      pix = 0;
       trel = 0;
+      inv = 0.f;
       outk = -1;
       if (i >= ns) return;
       if (rec) {
@@ -221,6 +252,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
         pix = __ldg(rpix + i);
         trel = (uint32_t)r.x;
         outk = r.y;
+        inv = 1.f;
         return;
       }
       int64_t k = i;
@@ -228,173 +260,200 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
         k = K[i];
         if (k < 0 || k >= ev.n) {
           if (lane < kRowsPerWarp) atomicOr(err, ERR_INDEX_RANGE);
-          outk = i | kInvalidRow;  // an invalid index's row gets zeros
+          outk = invalid_row(i);
           return;
         }
       }
       const int x = ev.x[k], y = ev.y[k];
       const uint32_t tt = ev.t[k];
       trel = tt - ev.t_ref;
-      if (x >= 0 && x < g.W && y >= 0 && y < g.H && tt >= ev.t_ref && trel <= ev.t_span)
+      if (x >= 0 && x < g.W && y >= 0 && y < g.H && tt >= ev.t_ref && trel <= ev.t_span) {
         pix = y * g.W + x;
-      outk = pix >= 0 ? i : (i | kInvalidRow);  // an invalid event's row gets zeros
+        outk = i;
+        inv = 1.f;
+      } else {
+        outk = invalid_row(i);
+      }
     };
-    int m_pix;
-    uint32_t m_trel;
-    int64_t m_outk;
-    if (nlocal > 0) meta(blockIdx.x, m_pix, m_trel, m_outk);
+    // (pixel, t - t_ref) of this warp's rows, two tiles: [tile parity][16]
+    int2 *ms = sMeta + pw * 2 * kRowsPerWarp;
+    const uint32_t sA_a = smem_u32(sA);
+    // FP16 grid: uint2 (half2 Re pair, half2 Im pair) per unit, already
+    // divided by n; FP32 grid: float4 (re 2u, im 2u, re 2u+1, im 2u+1)
+    using Q = typename std::conditional<HALF, uint2, float4>::type;
+    const Q *pooled = reinterpret_cast<const Q *>(pooled_v);
+    // rows per batch: the loads of one batch are in flight while the previous
+    // batch is computed (one batch of look-ahead, across tile boundaries)
+    constexpr int kB = HALF ? 8 / DV : 4 / DV;
+    constexpr int NB = kRowsPerWarp / kB;
+    static_assert(NB % 2 == 0, "batches alternate between two register sets");
+    Q qa[kB][DV], qb[kB][DV];
+    auto issue = [&](int par, int j0, Q(&q)[kB][DV]) {
+#pragma unroll
+      for (int r = 0; r < kB; ++r) {
+        const int pj = ms[par * kRowsPerWarp + j0 + r].x;
+#pragma unroll
+        for (int v = 0; v < DV; ++v) q[r][v] = __ldg(pooled + (size_t)pj * U + lane + 32 * v);
+      }
+    };
+    auto compute = [&](int par, int j0, const Q(&q)[kB][DV], uint32_t Abuf) {
+#pragma unroll
+      for (int r = 0; r < kB; ++r) {
+        const int j = j0 + r;
+        const uint32_t tj = (uint32_t)ms[par * kRowsPerWarp + j].y;
+#pragma unroll
+        for (int v = 0; v < DV; ++v) {
+          const float4 ph = time_phase2(tj, wf[v][0], wf[v][1]);  // (c0, s0, c1, s1)
+          uint32_t wre, wim;
+          if constexpr (HALF) {
+            // P conj(phase) in packed half2: Re = PR c + PI s, Im = PI c - PR s
+            const __half2 PR = *reinterpret_cast<const __half2 *>(&q[r][v].x);
+            const __half2 PI = *reinterpret_cast<const __half2 *>(&q[r][v].y);
+            const __half2 C = __floats2half2_rn(ph.x, ph.z);
+            const __half2 S = __floats2half2_rn(ph.y, ph.w);
+            const __half2 ER = __hfma2(PR, C, __hmul2(PI, S));
+            const __half2 EI = __hfma2(PI, C, __hneg2(__hmul2(PR, S)));
+            if (fp16) {
+              wre = *reinterpret_cast<const uint32_t *>(&ER);
+              wim = *reinterpret_cast<const uint32_t *>(&EI);
+            } else {
+              const float2 fr = __half22float2(ER), fi = __half22float2(EI);
+              wre = pack2(fr.x, fr.y, 0);
+              wim = pack2(fi.x, fi.y, 0);
+            }
+          } else {
+            const float4 e = cmul2c(q[r][v], ph);
+            wre = pack2(e.x, e.z, fp16);
+            wim = pack2(e.y, e.w, fp16);
+          }
+          const uint32_t addr = ((Abuf + lo[v]) ^ (uint32_t)((j & 7) * 0x90)) + (j >> 3) * 1024;
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(wre), "r"(wim) : "memory");
+        }
+      }
+    };
+    int c_outk = -1;
+    float c_inv = 0.f;
+    // pixels of this lane's row in the tile two ahead of the current one,
+    // whose pooled rows are prefetched into L2 (sorted path only)
+    int pf_pix = -1;
+    auto pf_load = [&](int t) {
+      const int i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
+      pf_pix = (rec && i < ns) ? __ldg(rpix + i) : -1;
+    };
+    if (nlocal > 0) {
+      int pix;
+      uint32_t trel;
+      meta(blockIdx.x, pix, trel, c_inv, c_outk);
+      if (!HALF && c_inv != 0.f) c_inv = 1.0f / (float)__ldg(ncnt + pix);
+      if (lane < kRowsPerWarp) ms[lane] = make_int2(pix, (int)trel);
+      __syncwarp();
+      issue(0, 0, qa);
+      pf_load((int)(blockIdx.x + 2 * gridDim.x));
+    }
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
-      const int64_t tile = blockIdx.x + (int64_t)li * gridDim.x;
+      const int tile = (int)blockIdx.x + li * (int)gridDim.x;
+      const bool has_next = li + 1 < nlocal;
+      int n_pix = 0;
+      uint32_t n_trel = 0;
+      float n_inv = 0.f;
+      int n_outk = -1;
+      if (has_next) meta(tile + (int)gridDim.x, n_pix, n_trel, n_inv, n_outk);
+      if (pf_pix >= 0) {  // L2 prefetch of this lane's half row of the tile after next
+        constexpr int kRowBytes = (HALF ? 8 : 16) * U;  // pooled bytes per pixel
+        constexpr int kHalfLines = kRowBytes / 256;      // 128-byte lines per half row
+        const char *row = reinterpret_cast<const char *>(pooled_v) + (size_t)pf_pix * kRowBytes;
+#pragma unroll
+        for (int l = 0; l < kHalfLines; ++l)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ((lane >> 4) * kHalfLines + l) * 128));
+      }
+      pf_load(tile + 3 * (int)gridDim.x);
       if (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1)) {
         ok = false;
         break;
       }
-      if (rec) {  // L2 prefetch of this warp's rows of the tile after next
-        const int64_t nt = tile + 2 * (int64_t)gridDim.x;
-        const int64_t i = nt * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
-        if (i < ns) {
-          const int p = __ldg(rpix + i);
-          constexpr int kRowBytes = (HALF ? 8 : 16) * U;  // pooled bytes per pixel
-          constexpr int kHalfLines = kRowBytes / 256;      // 128-byte lines per half row
-          const char *row = reinterpret_cast<const char *>(pooled_v) + (size_t)p * kRowBytes;
+      const uint32_t Abuf = sA_a + b * TILE_BYTES;
 #pragma unroll
-          for (int l = 0; l < kHalfLines; ++l)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ((lane >> 4) * kHalfLines + l) * 128));
+      for (int h = 0; h < NB; ++h) {
+        if (h + 1 < NB) {
+          if (h & 1) issue(b, (h + 1) * kB, qa);
+          else issue(b, (h + 1) * kB, qb);
+        } else if (has_next) {
+          __syncwarp();
+          if (lane < kRowsPerWarp) ms[(b ^ 1) * kRowsPerWarp + lane] = make_int2(n_pix, (int)n_trel);
+          __syncwarp();
+          issue(b ^ 1, 0, qa);
+          // FP32 grid: 1/n of the next tile's rows, consumed at that tile's end
+          if (!HALF && n_inv != 0.f) n_inv = 1.0f / (float)__ldg(ncnt + n_pix);
         }
+        if (h & 1) compute(b, h * kB, qb, Abuf);
+        else compute(b, h * kB, qa, Abuf);
       }
-      // lane j < 16 holds the metadata of row pw*16 + j (loaded one tile ahead)
-      const int pix = m_pix;
-      const uint32_t trel = m_trel;
-      const int64_t outk = m_outk;
-      if (li + 1 < nlocal) meta(tile + gridDim.x, m_pix, m_trel, m_outk);
+      // the epilogue reads these after the full barrier
       if (lane < kRowsPerWarp) {
-        sK[b * kM + pw * kRowsPerWarp + lane] = outk;
-        sInv[b * kM + pw * kRowsPerWarp + lane] =
-            pix < 0 ? 0.f : (HALF ? 1.f : 1.0f / (float)__ldg(ncnt + pix));
-      }
-      uint8_t *A = sA + b * TILE_BYTES;
-      // rows whose loads are issued together: 8 x 8 bytes per lane on the FP16
-      // grid, 4 x 16 bytes on the FP32 grid
-      constexpr int kB = HALF ? 8 / DV : 4 / DV;
-#pragma unroll
-      for (int j0 = 0; j0 < kRowsPerWarp; j0 += kB) {
-        // FP32 grid: float4 (re 2u, im 2u, re 2u+1, im 2u+1) per unit;
-        // FP16 grid: uint2 (half2 re pair, half2 im pair), already divided by n
-        float4 pv[kB][DV];
-        uint2 qv[kB][DV];
-        uint32_t tjs[kB];
-#pragma unroll
-        for (int r = 0; r < kB; ++r) {
-          const int pj = __shfl_sync(kFull, pix, j0 + r);
-          tjs[r] = __shfl_sync(kFull, trel, j0 + r);
-#pragma unroll
-          for (int v = 0; v < DV; ++v) {
-            if constexpr (HALF)
-              qv[r][v] = pj >= 0 ? __ldg(reinterpret_cast<const uint2 *>(pooled_v) +
-                                         (size_t)pj * U + lane + 32 * v)
-                                 : make_uint2(0u, 0u);
-            else
-              pv[r][v] = pj >= 0 ? __ldg(reinterpret_cast<const float4 *>(pooled_v) +
-                                         (size_t)pj * U + lane + 32 * v)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < kB; ++r) {
-          const int m = pw * kRowsPerWarp + j0 + r;
-          const uint32_t rowoff = (m >> 3) * 1024 + (m & 7) * 128;
-#pragma unroll
-          for (int v = 0; v < DV; ++v) {
-            const int u = lane + 32 * v;
-            const uint32_t kr = 2 * u, ki = D + 2 * u;
-            const uint32_t cr = (kr >> 6) * (kM * 128) + rowoff +
-                                ((((kr >> 3) & 7) ^ (m & 7)) << 4) + (kr & 7) * 2;
-            const uint32_t ci = (ki >> 6) * (kM * 128) + rowoff +
-                                ((((ki >> 3) & 7) ^ (m & 7)) << 4) + (ki & 7) * 2;
-            const float4 ph = time_phase2(tjs[r], wf[v][0], wf[v][1]);  // (c0, s0, c1, s1)
-            uint32_t wre, wim;
-            if constexpr (HALF) {
-              // packed half2: Re = PR C + PI S, Im = PI C - PR S (both channels at once)
-              const __half2 PR = *reinterpret_cast<const __half2 *>(&qv[r][v].x);
-              const __half2 PI = *reinterpret_cast<const __half2 *>(&qv[r][v].y);
-              const __half2 C = __floats2half2_rn(ph.x, ph.z);
-              const __half2 S = __floats2half2_rn(ph.y, ph.w);
-              const __half2 ER = __hfma2(PR, C, __hmul2(PI, S));
-              const __half2 EI = __hfma2(PI, C, __hneg2(__hmul2(PR, S)));
-              if (fp16) {
-                wre = *reinterpret_cast<const uint32_t *>(&ER);
-                wim = *reinterpret_cast<const uint32_t *>(&EI);
-              } else {
-                const float2 fr = __half22float2(ER), fi = __half22float2(EI);
-                wre = pack2(fr.x, fr.y, 0);
-                wim = pack2(fi.x, fi.y, 0);
-              }
-            } else {
-              const float4 e = cmul2c(pv[r][v], ph);
-              wre = pack2(e.x, e.z, fp16);
-              wim = pack2(e.y, e.w, fp16);
-            }
-            *reinterpret_cast<uint32_t *>(A + cr) = wre;
-            *reinterpret_cast<uint32_t *>(A + ci) = wim;
-          }
-        }
+        sK[b * kM + pw * kRowsPerWarp + lane] = c_outk;
+        sInv[b * kM + pw * kRowsPerWarp + lane] = c_inv;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(full_bar(b));
+      c_outk = n_outk;
+      c_inv = n_inv;
     }
-  } else if (warp == kMmaWarp) {
-    // ------------------------------------------------------------ MMA issuer
+  } else {
+    // ------------------------------------------------------------ epilogue
+    // (warp kMmaWarp issues each tile's MMAs first)
+    const int row = warp * 32 + lane;  // TMEM lane = tile row
+    const float b20 = mlp.b2[0], b21 = mlp.b2[1];
     constexpr uint32_t idesc_bf16 = make_idesc(0, kM, kN);
     constexpr uint32_t idesc_fp16 = make_idesc(1, kM, kN);
     const uint32_t idesc = fp16 ? idesc_fp16 : idesc_bf16;
     const uint32_t sA_a = smem_u32(sA), sB_a = smem_u32(sB);
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
-      if (!mbar_wait(full_bar(b), (li >> 1) & 1) ||
-          (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1))) {
+      // full: the producers' tile and row metadata
+      if (!mbar_wait(full_bar(b), (li >> 1) & 1)) {
         ok = false;
         break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (lane == 0) {
-        const uint32_t d_tmem = tmem + (uint32_t)(b * kN);
-        const uint32_t a_base = sA_a + b * TILE_BYTES;
+      if (warp == kMmaWarp) {
+        // accumulator b is free once all epilogue warps have read tile li - 2
+        if (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (lane == 0) {
+          const uint32_t d_tmem = tmem + (uint32_t)(b * kN);
+          const uint32_t a_base = sA_a + b * TILE_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < IN / 16; ++kk) {
-          // K-step kk: K-block kk / 4, 32-byte step kk % 4 inside the swizzle atom
-          const uint32_t koff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
-          const uint64_t ad = make_desc_sw128(a_base + koff);
-          const uint64_t bd = make_desc_sw128(sB_a + koff);
-          const uint32_t acc = kk > 0 ? 1u : 0u;
+          for (int kk = 0; kk < IN / 16; ++kk) {
+            // K-step kk: K-block kk / 4, 32-byte step kk % 4 inside the swizzle atom
+            const uint32_t koff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
+            const uint64_t ad = make_desc_sw128(a_base + koff);
+            const uint64_t bd = make_desc_sw128(sB_a + koff);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
           asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  done_bar(b))
               : "memory");
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                done_bar(b))
-            : "memory");
+        __syncwarp();
       }
-      __syncwarp();
-    }
-  } else {
-    // ------------------------------------------------------------ epilogue
-    const int row = warp * 32 + lane;  // TMEM lane = tile row
-    const float b20 = mlp.b2[0], b21 = mlp.b2[1];
-    for (int li = 0; li < nlocal && ok; ++li) {
-      const int b = li & 1;
-      // full: the producers' row metadata; done: the accumulator
-      if (!mbar_wait(full_bar(b), (li >> 1) & 1) || !mbar_wait(done_bar(b), (li >> 1) & 1)) {
+      // done: the accumulator
+      if (!mbar_wait(done_bar(b), (li >> 1) & 1)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float inv = sInv[b * kM + row];
-      const int64_t k = sK[b * kM + row];
+      const int k = sK[b * kM + row];
       // packed FP32x2 arithmetic: even and odd columns in the two halves
       float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
       const float2 inv2 = make_float2(inv, inv);
@@ -422,9 +481,10 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(empty_bar(b));
       if (k >= 0) {
-        const bool valid = !(k & kInvalidRow);
-        *reinterpret_cast<float2 *>(flow + 2 * (k & ~kInvalidRow)) =
-            valid ? make_float2(o0.x + o0.y + b20, o1.x + o1.y + b21) : make_float2(0.f, 0.f);
+        *reinterpret_cast<float2 *>(flow + 2 * (size_t)k) =
+            make_float2(o0.x + o0.y + b20, o1.x + o1.y + b21);
+      } else if (k <= -2) {
+        *reinterpret_cast<float2 *>(flow + 2 * (size_t)(-2 - k)) = make_float2(0.f, 0.f);
       }
     }
   }
@@ -450,7 +510,8 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
   const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (3 * kN + 2 * kM) +
-                    sizeof(int64_t) * 2 * kM + 8 * 6 + 16 + 1024;  // + SW128 alignment slack
+                    sizeof(int) * 2 * kM + 8 * 6 + sizeof(int2) * kProdWarps * 2 * kRowsPerWarp +
+                    16 + 1024;  // + SW128 alignment slack
   auto kern = k_predict_tc<DV, HALF>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
           cudaSuccess ||

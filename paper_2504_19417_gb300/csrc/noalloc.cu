@@ -64,6 +64,8 @@ extern "C" veckm_status veckm_encode_noalloc(veckm_ctx *ctx, const int16_t *d_x,
     return report(VECKM_EINVAL,
                   "veckm_encode_noalloc takes at most 1048576 events per call "
                   "(its static record array); use veckm_encode for larger slices");
+  if (nK > VECKM_MAX_EVENTS)
+    return report(VECKM_EINVAL, "more than 2^30 requested events in one call");
   if (n > 0 && (!d_x || !d_y || !d_t)) return report(VECKM_EINVAL, "null event buffer");
   if (!d_K && nK != n && nK != 0) return report(VECKM_EINVAL, "K is NULL but nK != n");
   if (nK > 0 && !d_emb) return report(VECKM_EINVAL, "null output buffer");

@@ -17,13 +17,15 @@ namespace veckm {
 
 // exp(i 2 pi t w) for one channel, w64 = (whi << 32) | wlo.
 __device__ __forceinline__ float2 turn_phase(uint32_t t, uint32_t wlo, uint32_t whi) {
-  // top 32 bits of t * w64 (mod 2^64), plus half a unit of the 23-bit fraction below
-  const uint32_t fr = __umulhi(t, wlo) + t * whi + 256u;
-  // 1.f with the 23-bit turn fraction as mantissa, minus 1.5: turn - 1/2 in [-1/2, 1/2)
+  // top 32 bits of t * w64 + 1/2 turn (mod 2^64), plus half a unit of the
+  // 23-bit fraction kept below: fr / 2^32 = frac(t w + 1/2)
+  const uint32_t fr = __umulhi(t, wlo) + t * whi + 0x80000100u;
+  // 1.f with that fraction as mantissa, minus 1.5: frac(t w + 1/2) - 1/2, which
+  // lies in [-1/2, 1/2) and equals t w modulo whole turns
   const float f = __uint_as_float(0x3f800000u | (fr >> 9)) - 1.5f;
   float s, c;
-  __sincosf(f * 6.28318530717958647692f, &s, &c);  // angle - pi
-  return make_float2(-c, -s);                        // exp(i angle) = -exp(i (angle - pi))
+  __sincosf(f * 6.28318530717958647692f, &s, &c);
+  return make_float2(c, s);
 }
 
 // Channels 2u and 2u+1 as one float4 (re0, im0, re1, im1); w holds their

@@ -120,13 +120,21 @@ uint16_t half_bits(float v, bool fp16) {
 // W1 [hidden][IN] -> the K-major 128-byte-swizzled order the tcgen05 kernel
 // reads: K-blocks of 64 columns, each hidden x 128 B; row n of a block at
 // (n/8)*1024 + (n%8)*128, its 16-byte chunk c at position c ^ (n%8).
+// W1 as the tensor-core B operand: K-major, 128-byte swizzled, with the K
+// axis permuted to the order in which the gather writes the A operand: K
+// position 4u + {0, 1, 2, 3} holds input Re(2u), Re(2u+1), Im(2u), Im(2u+1),
+// i.e. columns 2u, 2u+1, D+2u, D+2u+1 of W1 (whose input is packed [Re | Im]).
+// The contraction runs over all of K, so the same permutation of A's columns
+// and B's rows leaves W1 x unchanged.
 std::vector<uint16_t> w1_core_matrix(const std::vector<float> &W1, int hidden, int IN, bool fp16) {
   std::vector<uint16_t> out((size_t)hidden * IN);
+  const int D = IN / 2;
   for (int n = 0; n < hidden; ++n)
     for (int k = 0; k < IN; ++k) {
+      const int src = ((k & 2) ? D : 0) + 2 * (k >> 2) + (k & 1);
       const size_t byte = (size_t)(k / 64) * hidden * 128 + (size_t)(n / 8) * 1024 + (n % 8) * 128 +
                           (size_t)((((k / 8) % 8) ^ (n % 8)) * 16) + (k % 8) * 2;
-      out[byte / 2] = half_bits(W1[(size_t)n * IN + k], fp16);
+      out[byte / 2] = half_bits(W1[(size_t)n * IN + src], fp16);
     }
   return out;
 }
@@ -158,12 +166,14 @@ veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const
                                int64_t n, const void *K, int64_t nK, const void *out) {
   if (!c) return fail(VECKM_EINVAL, "null context");
   if (n < 0 || nK < 0) return fail(VECKM_EINVAL, "negative size (n=%lld, nK=%lld)", (long long)n, (long long)nK);
+  if (n > VECKM_MAX_EVENTS || nK > VECKM_MAX_EVENTS)
+    return fail(VECKM_EINVAL, "more than %lld events or requests in one call (n=%lld, nK=%lld)",
+                (long long)VECKM_MAX_EVENTS, (long long)n, (long long)nK);
   if (n > 0 && (!x || !y || !t)) return fail(VECKM_EINVAL, "null event buffer with n=%lld", (long long)n);
   if (!K && nK != n && nK != 0)
     return fail(VECKM_EINVAL, "K is NULL but nK (%lld) != n (%lld)", (long long)nK, (long long)n);
   if (nK > 0 && !out) return fail(VECKM_EINVAL, "null output buffer");
   if (nK > 0 && n == 0) return fail(VECKM_EINVAL, "nK > 0 with an empty slice");
-  if (n >= (int64_t)1 << 31) return fail(VECKM_EINVAL, "n too large (%lld)", (long long)n);
   return VECKM_OK;
 }
 

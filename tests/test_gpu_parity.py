@@ -157,6 +157,25 @@ def test_empty_inputs():
     enc.sync_status()
 
 
+def test_oversized_call_is_rejected_before_any_device_work():
+    # the size check comes before every other argument check and any launch,
+    # so the claimed n never reaches the device
+    import ctypes as C
+    sl = synth.event_slice(50, 40, 100, 1_000, seed=1)
+    enc, _, _ = make(sl, 64)
+    x, y, t = to_dev(sl)
+    out = torch.empty((4, 2), dtype=torch.float32, device="cuda")
+    big = (1 << 30) + 1
+    lib = vk.lib()
+    for fn in (lib.veckm_encode, lib.veckm_predict, lib.veckm_encode_noalloc):
+        st = fn(enc.handle, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                C.c_void_p(t.data_ptr()), big, C.c_uint32(sl.t_ref), None, big,
+                C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == vk.VECKM_EINVAL
+    assert b"events" in lib.veckm_last_error()
+    enc.sync_status()
+
+
 def test_out_of_range_event_reports_erange_and_skips_it():
     sl = synth.event_slice(60, 50, 2_000, 10_000, seed=3)
     enc, TXY, _ = make(sl, 64, t_span_us=10_000)
