@@ -177,6 +177,78 @@ veckm_status veckm_stage_times(veckm_ctx *ctx, double *ms, int64_t *calls, int n
 /* Number of kernel launches the last encode/predict call made. */
 int veckm_last_launch_count(const veckm_ctx *ctx);
 
+/* ------------------------------------------------------------------ batches
+ * Several slices, possibly from sensors of different sizes, encoded in one
+ * pass.  The library lays the sensors out on a canvas, one large virtual
+ * sensor of at most the context's width x height, each sensor at an offset
+ * (ox, oy) and at least dx empty columns and dy empty rows away from any
+ * other.  The encoding of Eq. emb depends on pixel coordinates only through
+ * differences inside a (2dx+1) x (2dy+1) window, so a shifted sensor encodes
+ * exactly as on its own, and no window reaches another sensor.  Times enter
+ * only as differences inside a window too, so each slice keeps its own start
+ * t_ref_us.  The canvas then goes through the encoder once: one launch per
+ * stage for the whole batch.  Not in the paper (which encodes one slice at a
+ * time); results equal those of per-slice calls up to FP32 summation order. */
+typedef struct {
+    const int16_t *d_x, *d_y; /* device, n events each */
+    const uint32_t *d_t;      /* device, microseconds; every t in [t_ref_us, t_ref_us + t_span] */
+    int64_t n;                /* events of this slice (0 allowed) */
+    uint32_t t_ref_us;        /* slice start */
+    int32_t width, height;    /* this slice's sensor; each at most the context's */
+} veckm_slice;
+
+/* Host-only shelf packing used by the batch calls: sensors sorted by height
+ * (ties by index), placed left to right in shelves no wider than max_width,
+ * with gap_x columns between neighbours and gap_y rows between shelves.
+ * Writes each sensor's offset to ox[i], oy[i] and the canvas extent (the
+ * bounding box of all sensors) to *canvas_w, *canvas_h.  VECKM_EINVAL if a
+ * sensor is wider than max_width or a size is not positive. */
+veckm_status veckm_canvas_layout(int32_t nslices, const int32_t *widths, const int32_t *heights,
+                                 int32_t gap_x, int32_t gap_y, int32_t max_width, int32_t *ox,
+                                 int32_t *oy, int32_t *canvas_w, int32_t *canvas_h);
+
+/* Flows of every event of every slice: d_flow (device) is float
+ * [sum n][2], slices in order, events in input order within a slice.
+ * VECKM_EBUSY if the canvas does not fit the context (width x height) or the
+ * records cannot grow while a plan exists.  Out-of-range events are reported
+ * as in veckm_predict (their rows are zeroed).  May grow context buffers with
+ * cudaMalloc (synchronising the stream) the first time a larger batch comes. */
+veckm_status veckm_predict_batch(veckm_ctx *ctx, const veckm_slice *slices, int32_t nslices,
+                                 float *d_flow, void *stream);
+/* Encodings of every event of every slice: d_emb is float [sum n][2D]. */
+veckm_status veckm_encode_batch(veckm_ctx *ctx, const veckm_slice *slices, int32_t nslices,
+                                float *d_emb, void *stream);
+
+/* A batch captured once into a CUDA graph and replayed: the slices' buffers,
+ * sizes and starts and the output buffer are fixed at creation (new event
+ * values in the same buffers are picked up by each launch).  Creation
+ * allocates what the batch needs, autotunes the pooling launch shapes for its
+ * canvas if veckm_autotune has not, and captures every copy and kernel of the
+ * batch call on an internal stream.  predict != 0 captures
+ * veckm_predict_batch, else veckm_encode_batch.  While a plan exists its
+ * context keeps its buffers (calls needing larger ones return VECKM_EBUSY) and
+ * its precision (veckm_set_mlp_mode returns VECKM_EBUSY).  A plan must be
+ * destroyed before its context. */
+typedef struct veckm_plan veckm_plan;
+veckm_status veckm_plan_create(veckm_ctx *ctx, const veckm_slice *slices, int32_t nslices,
+                               float *d_out, int32_t predict, veckm_plan **out);
+/* Launch the captured graph on stream (ordered after earlier work there). */
+veckm_status veckm_plan_launch(veckm_plan *plan, void *stream);
+/* Number of kernel launches in one replay of the plan. */
+int veckm_plan_kernel_count(const veckm_plan *plan);
+void veckm_plan_destroy(veckm_plan *plan);
+
+/* Autotune the launch shapes of the pooling passes (segment length per warp
+ * and warps per block of the row and column passes) for a width x height
+ * geometry (at most the context's): every candidate is timed with CUDA
+ * events on stream over the context's accumulator buffers, and the fastest
+ * is kept for calls on that geometry and pooled-grid storage.  Overwrites the
+ * context's intermediate buffers (not the caller's).  Synchronous.  The
+ * choice never changes results.  Writes the chosen shapes to tuned[0..3]
+ * (rows segment, rows warps, columns segment, columns warps) if non-NULL. */
+veckm_status veckm_autotune(veckm_ctx *ctx, int32_t width, int32_t height, void *stream,
+                            int32_t *tuned);
+
 /* SplitMix64 + Box-Muller standard normals (the generator behind freq_seed):
  * writes count normals of stream `seed` to h_out.  Host only. */
 void veckm_normals(uint64_t seed, int64_t count, double *h_out);

@@ -1,0 +1,86 @@
+// The context behind the veckm_ctx handle of the C ABI (private to the
+// library's translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "veckm_internal.h"
+
+namespace veckm {
+constexpr int kStages = 6;  // sort, pixel sums, pool rows, counts, pool cols, gather
+}  // namespace veckm
+
+struct veckm_ctx {
+  int device = 0;
+  veckm::Geometry g{};
+  int hidden = 0;
+  uint32_t flags = 0;
+  int64_t dt_us = 0, t_span = 0;
+  double sigma2 = 25.0;
+  std::vector<double> T, X, Y;
+  // device state
+  float4 *tx = nullptr, *ty = nullptr, *sx = nullptr, *sy = nullptr;
+  uint2 *wt = nullptr;
+  float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
+  uint16_t *W1h = nullptr;
+  float4 *acc = nullptr, *hbuf = nullptr;
+  int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
+  int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
+  // pixel-sorted event records (grown on demand)
+  int2 *rec = nullptr;
+  int *rpix = nullptr;
+  int64_t rec_cap = 0;
+  std::vector<float> hW1;  // host copy (re-encoding on precision switch)
+  // staging for the host-buffer entry point
+  void *st_buf = nullptr;
+  size_t st_cap = 0;
+  int *h_err = nullptr;  // pinned
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::vector<cudaEvent_t>> pending;
+  double stage_ms[veckm::kStages] = {};
+  int64_t stage_launch[veckm::kStages] = {};
+  int last_launches = 0;
+
+  // autotuned launch shapes per geometry and pooled-grid storage
+  struct TuneEntry {
+    int W, H;
+    uint32_t acc16;
+    veckm::Tune tn;
+  };
+  std::vector<TuneEntry> tunes;
+  // batches: canvas events (grown on demand), the device slice table and a
+  // pinned host copy for direct batch calls
+  int16_t *cx = nullptr, *cy = nullptr;
+  uint32_t *ct = nullptr;
+  int64_t canvas_cap = 0;
+  void *slice_tab = nullptr, *h_slice_tab = nullptr;
+  size_t slice_tab_cap = 0, h_slice_tab_cap = 0;
+  cudaEvent_t tab_copied = nullptr;  // the last copy out of h_slice_tab
+  int live_plans = 0;                // captured graphs that use this context's buffers
+
+  veckm::Tables tables() const { return veckm::Tables{tx, ty, sx, sy, wt}; }
+  veckm::Tune tune_for(const veckm::Geometry &gg) const {
+    for (const TuneEntry &t : tunes)
+      if (t.W == gg.W && t.H == gg.H && t.acc16 == (flags & VECKM_ACC_FP16)) return t.tn;
+    return veckm::Tune{};
+  }
+  veckm::MLP mlp() const {
+    return veckm::MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0};
+  }
+};
+
+namespace veckm {
+// Grows the pixel-sorted record buffers to n events (synchronises the stream
+// when it reallocates); VECKM_EBUSY while captured plans hold the old ones.
+veckm_status ensure_records(veckm_ctx *c, int64_t n, cudaStream_t s);
+// The encoder (flow: and the perceptron) for the events ev on geometry g: a
+// sensor, or a canvas of packed sensors no larger than the context's.
+veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, const int64_t *K,
+                          int64_t nK, float *out, bool flow, cudaStream_t s, const Tune &tn);
+// Error helpers shared by the entry points (veckm.cu).
+veckm_status fail_msg(veckm_status st, const char *fmt, ...);
+veckm_status fail_cuda(cudaError_t e, const char *what);
+}  // namespace veckm

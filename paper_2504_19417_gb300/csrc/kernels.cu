@@ -343,7 +343,7 @@ enum class Pass { Rows, Cols };
 // n (Eq. 17; 0 where the window is empty) and stored as FP16, unit u of a
 // pixel = 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
 template <int DV, Pass P, bool HALF = false>
-__global__ void __launch_bounds__(64) k_box_pass(const float4 *__restrict__ src,
+__global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
                                                  int seg, int nseg,
                                                  const int *__restrict__ ncnt = nullptr) {
@@ -736,17 +736,22 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
+// Largest dynamic shared memory a box-pass block may ask for.
+constexpr size_t kBoxSmemMax = 200 * 1024;
+
 template <int DV, Pass P, bool HALF = false>
 int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s,
-             const int *ncnt = nullptr) {
+             const int *ncnt, int seg_windows, int wpb_req) {
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
   const int L = 2 * r + 1;
   const int len = (P == Pass::Rows) ? g.W : g.H;
   const int nlines = (P == Pass::Rows) ? g.H : g.W;
-  const int seg = L * std::max(1, (128 + L / 2) / L);
+  // a warp walks `seg` outputs of one line (a whole number of windows)
+  const int seg = L * (seg_windows > 0 ? seg_windows : std::max(1, (128 + L / 2) / L));
   const int nseg = (len + seg - 1) / seg;
   const size_t per_warp = (size_t)3 * (L + 1) * 32 * DV * sizeof(float4);
-  const int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
+  int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
+  if (wpb_req > 0 && wpb_req <= 4 && per_warp * wpb_req <= kBoxSmemMax) wpb = wpb_req;
   const size_t sm = per_warp * wpb;
   if (set_smem(k_box_pass<DV, P, HALF>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
@@ -855,20 +860,22 @@ int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const
 }
 
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
-                     cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Rows>(g, tb, acc, hbuf, s)));
+                     cudaStream_t s, const Tune &tn) {
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Rows>(g, tb, acc, hbuf, s, nullptr, tn.rows_seg,
+                                                   tn.rows_wpb)));
 }
 
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
-                     cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols>(g, tb, hbuf, acc, s)));
+                     cudaStream_t s, const Tune &tn) {
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols>(g, tb, hbuf, acc, s, nullptr, tn.cols_seg,
+                                                   tn.cols_wpb)));
 }
 
 int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbuf,
-                          const int *ncnt, void *pooled16, cudaStream_t s) {
+                          const int *ncnt, void *pooled16, cudaStream_t s, const Tune &tn) {
   VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, true>(g, tb, hbuf,
                                                          reinterpret_cast<float4 *>(pooled16), s,
-                                                         ncnt)));
+                                                         ncnt, tn.cols_seg, tn.cols_wpb)));
 }
 
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s) {

@@ -506,7 +506,7 @@ template <int DV, bool HALF>
 int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                     const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                     const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
-                    cudaStream_t s) {
+                    cudaStream_t s, int ctas_req) {
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
   const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (3 * kN + 2 * kM) +
@@ -518,7 +518,8 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
       cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return -1;
-  const int per_sm = std::min(blocks_per_sm((const void *)kern, kThreads, sm), 512 / kTmemCols);
+  int per_sm = std::min(blocks_per_sm((const void *)kern, kThreads, sm), 512 / kTmemCols);
+  if (ctas_req > 0) per_sm = std::min(per_sm, ctas_req);
   const int64_t tiles = (nK + kM - 1) / kM;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm);
   kern<<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
@@ -531,15 +532,15 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
-                      int *err, cudaStream_t s) {
+                      int *err, cudaStream_t s, const Tune &tn) {
   const bool h = mlp.pooled_half != 0;
   switch (g.U / 32) {
     case 1:
-      return h ? predict_tc_impl<1, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s)
-               : predict_tc_impl<1, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
+      return h ? predict_tc_impl<1, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas)
+               : predict_tc_impl<1, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas);
     case 2:
-      return h ? predict_tc_impl<2, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s)
-               : predict_tc_impl<2, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s);
+      return h ? predict_tc_impl<2, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas)
+               : predict_tc_impl<2, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas);
     default:
       return -1;  // 2D > 256 does not fit the operand tiles in shared memory
   }

@@ -13,7 +13,7 @@
 #include <new>
 #include <vector>
 
-#include "veckm_internal.h"
+#include "ctx.h"
 
 using namespace veckm;
 
@@ -42,48 +42,9 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
-constexpr int kStages = 6;  // sort, pixel sums, pool rows, counts, pool cols, gather
+enum class Out { Emb, Flow };
 
 }  // namespace
-
-struct veckm_ctx {
-  int device = 0;
-  Geometry g{};
-  int hidden = 0;
-  uint32_t flags = 0;
-  int64_t dt_us = 0, t_span = 0;
-  double sigma2 = 25.0;
-  std::vector<double> T, X, Y;
-  // device state
-  float4 *tx = nullptr, *ty = nullptr, *sx = nullptr, *sy = nullptr;
-  uint2 *wt = nullptr;
-  float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
-  uint16_t *W1h = nullptr;
-  float4 *acc = nullptr, *hbuf = nullptr;
-  int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
-  int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
-  // pixel-sorted event records (grown on demand)
-  int2 *rec = nullptr;
-  int *rpix = nullptr;
-  int64_t rec_cap = 0;
-  std::vector<float> hW1;  // host copy (re-encoding on precision switch)
-  // staging for the host-buffer entry point
-  void *st_buf = nullptr;
-  size_t st_cap = 0;
-  int *h_err = nullptr;  // pinned
-  // timing
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_free;
-  std::vector<std::vector<cudaEvent_t>> pending;
-  double stage_ms[kStages] = {};
-  int64_t stage_launch[kStages] = {};
-  int last_launches = 0;
-
-  Tables tables() const { return Tables{tx, ty, sx, sy, wt}; }
-  MLP mlp() const {
-    return MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0};
-  }
-};
 
 namespace {
 
@@ -142,10 +103,13 @@ std::vector<uint16_t> w1_core_matrix(const std::vector<float> &W1, int hidden, i
 void free_all(veckm_ctx *c) {
   void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
                   c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
-                  c->off, c->cur, c->bsum, c->total, c->rec, c->rpix};
+                  c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->cx, c->cy, c->ct,
+                  c->slice_tab};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->h_slice_tab) cudaFreeHost(c->h_slice_tab);
+  if (c->tab_copied) cudaEventDestroy(c->tab_copied);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   for (auto &v : c->pending)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -177,16 +141,37 @@ veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const
   return VECKM_OK;
 }
 
-enum class Out { Emb, Flow };
+}  // namespace
 
-veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_t *t, int64_t n,
-                 uint32_t t_ref, const int64_t *K, int64_t nK, float *out, cudaStream_t s, Out what) {
-  veckm_status st = check_events_args(c, x, y, t, n, K, nK, out);
-  if (st) return st;
+namespace veckm {
+
+veckm_status ensure_records(veckm_ctx *c, int64_t n, cudaStream_t s) {
+  if (n <= c->rec_cap) return VECKM_OK;
+  if (c->live_plans > 0)
+    return fail(VECKM_EBUSY, "%lld events need larger record buffers, which cannot be "
+                "reallocated while a captured plan uses them", (long long)n);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (c->rec) cudaFree(c->rec);
+  if (c->rpix) cudaFree(c->rpix);
+  c->rec = nullptr;
+  c->rpix = nullptr;
+  c->rec_cap = 0;
+  if (e == cudaSuccess) e = dalloc(&c->rec, (size_t)n);
+  if (e == cudaSuccess) e = dalloc(&c->rpix, (size_t)n);
+  if (e != cudaSuccess) return cuda_fail(e, "event record buffers");
+  c->rec_cap = n;
+  return VECKM_OK;
+}
+
+veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, const int64_t *K,
+                          int64_t nK, float *out, bool flow, cudaStream_t s, const Tune &tn) {
+  const Out what = flow ? Out::Flow : Out::Emb;
+  const int64_t n = ev.n;
   c->last_launches = 0;
   if (nK == 0) return VECKM_OK;  // nothing requested: no work
-  const Geometry &g = c->g;
-  const Events ev{x, y, t, n, t_ref, (uint32_t)c->t_span};
+  if ((int64_t)g.W * g.H > (int64_t)c->g.W * c->g.H || g.W > c->g.W || g.H > c->g.H)
+    return fail(VECKM_EINVAL, "geometry %dx%d exceeds the context's %dx%d", g.W, g.H, c->g.W,
+                c->g.H);
   const Tables tb = c->tables();
   std::vector<cudaEvent_t> evs;
   auto mark = [&]() {
@@ -199,18 +184,7 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
   const size_t P = (size_t)g.W * g.H;
   // pixel-sorted prediction for "all events"; explicit K keeps input order
   const bool sorted = (what == Out::Flow) && K == nullptr;
-  if (n > c->rec_cap) {
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (c->rec) cudaFree(c->rec);
-    if (c->rpix) cudaFree(c->rpix);
-    c->rec = nullptr;
-    c->rpix = nullptr;
-    c->rec_cap = 0;
-    if (e == cudaSuccess) e = dalloc(&c->rec, (size_t)n);
-    if (e == cudaSuccess) e = dalloc(&c->rpix, (size_t)n);
-    if (e != cudaSuccess) return cuda_fail(e, "event record buffers");
-    c->rec_cap = n;
-  }
+  if (veckm_status st = ensure_records(c, n, s)) return st;
   int launches = 0, r;
   mark();
   cudaError_t e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
@@ -229,7 +203,7 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
   mark();
-  if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, s)) < 0)
+  if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, s, tn)) < 0)
     return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   mark();
@@ -240,9 +214,9 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
   // FP16 storage of the normalised pooled grid serves the tensor-core head only
   const bool half_grid = what == Out::Flow && (c->flags & VECKM_ACC_FP16);
   if (half_grid)
-    r = launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, s);
+    r = launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, s, tn);
   else
-    r = launch_pool_cols(g, tb, c->hbuf, c->acc, s);
+    r = launch_pool_cols(g, tb, c->hbuf, c->acc, s, tn);
   if (r < 0) return cuda_fail(cudaGetLastError(), "pooling (columns) launch");
   launches += r;
   mark();
@@ -252,7 +226,7 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
     MLP m = c->mlp();
     m.pooled_half = half_grid ? 1 : 0;
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
-                          c->off + P, g, tb, c->acc, c->ncnt, m, out, c->err, s);
+                          c->off + P, g, tb, c->acc, c->ncnt, m, out, c->err, s, tn);
   } else {
     r = launch_predict_fp32(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
                             c->off + P, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
@@ -264,6 +238,18 @@ veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_
   if (c->timing) c->pending.push_back(evs);
   c->last_launches = launches;
   return VECKM_OK;
+}
+
+}  // namespace veckm
+
+namespace {
+
+veckm_status run(veckm_ctx *c, const int16_t *x, const int16_t *y, const uint32_t *t, int64_t n,
+                 uint32_t t_ref, const int64_t *K, int64_t nK, float *out, cudaStream_t s, Out what) {
+  veckm_status st = check_events_args(c, x, y, t, n, K, nK, out);
+  if (st) return st;
+  const Events ev{x, y, t, n, t_ref, (uint32_t)c->t_span};
+  return run_pipeline(c, c->g, ev, K, nK, out, what == Out::Flow, s, c->tune_for(c->g));
 }
 
 bool valid_D(int D) { return D == 64 || D == 128 || D == 192 || D == 256; }
@@ -424,6 +410,7 @@ void veckm_destroy(veckm_ctx *c) {
 
 veckm_status veckm_set_mlp_mode(veckm_ctx *c, uint32_t flags) {
   if (!c) return fail(VECKM_EINVAL, "null context");
+  if (c->live_plans > 0) return fail(VECKM_EBUSY, "captured plans use this context's mode");
   const uint32_t known = VECKM_MLP_BF16 | VECKM_MLP_FP16;
   if ((flags & ~(known | VECKM_ACC_FP16)) || ((flags & VECKM_MLP_BF16) && (flags & VECKM_MLP_FP16)) ||
       ((flags & VECKM_ACC_FP16) && !(flags & known)))
@@ -574,5 +561,15 @@ bool ctx_view(const veckm_ctx *c, CtxView *v) {
 }
 
 veckm_status report(veckm_status st, const char *msg) { return fail(st, "%s", msg); }
+
+veckm_status fail_msg(veckm_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+veckm_status fail_cuda(cudaError_t e, const char *what) { return cuda_fail(e, what); }
 
 }  // namespace veckm

@@ -47,6 +47,14 @@ struct MLP {
   int pooled_half;       // 1: the pooled grid is FP16 and already divided by the counts
 };
 
+// Launch shapes picked by the autotuner (batch.cu); 0 keeps the built-in
+// default.  The results do not depend on them.
+struct Tune {
+  int rows_seg = 0, rows_wpb = 0;  // row pass: segment length in windows, warps per block
+  int cols_seg = 0, cols_wpb = 0;  // column pass: the same
+  int tc_ctas = 0;                 // tensor-core head: CTAs per SM (1 or 2)
+};
+
 // Launchers (kernels.cu, mlp_tc.cu).  Each returns the number of kernels it
 // launched, or a negative value on a launch failure.
 // zero_flow (nullable): flow rows of invalid events are zeroed (sorted prediction).
@@ -64,14 +72,14 @@ int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const
 int blocks_per_sm(const void *func, int threads, size_t smem);
 // Pooling: row pass acc -> hbuf, column pass hbuf -> acc, window counts.
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
-                     cudaStream_t s);
+                     cudaStream_t s, const Tune &tn = Tune{});
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
-                     cudaStream_t s);
+                     cudaStream_t s, const Tune &tn = Tune{});
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s);
 // Column pass writing the pooled grid divided by the window counts as FP16:
 // per pixel D/2 units of 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
 int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbuf,
-                          const int *ncnt, void *pooled16, cudaStream_t s);
+                          const int *ncnt, void *pooled16, cudaStream_t s, const Tune &tn = Tune{});
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                       const Tables &tb, const float4 *pooled, const int *ncnt, float *emb,
                       int *err, cudaStream_t s);
@@ -86,7 +94,7 @@ int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const in
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
-                      int *err, cudaStream_t s);
+                      int *err, cudaStream_t s, const Tune &tn = Tune{});
 
 int num_sms();
 

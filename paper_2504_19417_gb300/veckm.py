@@ -42,10 +42,17 @@ class _Config(C.Structure):
                 ("h_W2", C.c_void_p), ("h_b2", C.c_void_p), ("flags", C.c_uint32)]
 
 
+class _Slice(C.Structure):
+    _fields_ = [("d_x", C.c_void_p), ("d_y", C.c_void_p), ("d_t", C.c_void_p), ("n", C.c_int64),
+                ("t_ref_us", C.c_uint32), ("width", C.c_int32), ("height", C.c_int32)]
+
+
 EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noalloc", "veckm_predict",
            "veckm_predict_host", "veckm_set_mlp_mode", "veckm_sync_status", "veckm_last_error",
            "veckm_get_frequencies", "veckm_set_timing", "veckm_stage_times",
-           "veckm_last_launch_count", "veckm_normals")
+           "veckm_last_launch_count", "veckm_canvas_layout", "veckm_predict_batch",
+           "veckm_encode_batch", "veckm_plan_create", "veckm_plan_launch",
+           "veckm_plan_kernel_count", "veckm_plan_destroy", "veckm_autotune", "veckm_normals")
 
 
 def library_path() -> str:
@@ -75,9 +82,22 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_last_launch_count.argtypes = [P]
     lib.veckm_normals.argtypes = [C.c_uint64, i64, P]
     lib.veckm_normals.restype = None
+    i32 = C.c_int32
+    lib.veckm_canvas_layout.argtypes = [i32, P, P, i32, i32, i32, P, P, P, P]
+    lib.veckm_predict_batch.argtypes = [P, P, i32, P, P]
+    lib.veckm_encode_batch.argtypes = [P, P, i32, P, P]
+    lib.veckm_plan_create.argtypes = [P, P, i32, P, i32, C.POINTER(C.c_void_p)]
+    lib.veckm_plan_launch.argtypes = [P, P]
+    lib.veckm_plan_kernel_count.argtypes = [P]
+    lib.veckm_plan_destroy.argtypes = [P]
+    lib.veckm_plan_destroy.restype = None
+    lib.veckm_autotune.argtypes = [P, i32, i32, P, P]
     for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
                  "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
-                 "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count"):
+                 "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count",
+                 "veckm_canvas_layout", "veckm_predict_batch", "veckm_encode_batch",
+                 "veckm_plan_create", "veckm_plan_launch", "veckm_plan_kernel_count",
+                 "veckm_autotune"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -105,6 +125,75 @@ def normals(seed: int, count: int) -> np.ndarray:
     out = np.zeros(count, np.float64)
     lib().veckm_normals(C.c_uint64(seed), count, _np_ptr(out))
     return out
+
+
+def canvas_layout(widths, heights, gap_x: int, gap_y: int, max_width: int):
+    """Shelf packing of sensors on a canvas: (ox, oy, canvas_w, canvas_h)."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    h = np.ascontiguousarray(heights, dtype=np.int32)
+    ox = np.zeros(w.size, np.int32)
+    oy = np.zeros(w.size, np.int32)
+    cw, ch = C.c_int32(), C.c_int32()
+    _check(lib().veckm_canvas_layout(w.size, _np_ptr(w), _np_ptr(h), gap_x, gap_y, max_width,
+                                     _np_ptr(ox), _np_ptr(oy), C.byref(cw), C.byref(ch)))
+    return ox, oy, cw.value, ch.value
+
+
+@dataclass
+class Slice:
+    """One slice of a batch: int16 x, y and int32 (uint32 bits) t CUDA tensors."""
+    x: object
+    y: object
+    t: object
+    t_ref: int
+    width: int
+    height: int
+
+    @property
+    def n(self) -> int:
+        return int(self.x.numel())
+
+
+def _slice_array(slices):
+    arr = (_Slice * max(1, len(slices)))()
+    for i, s in enumerate(slices):
+        n = s.n
+        arr[i] = _Slice(s.x.data_ptr() if n else None, s.y.data_ptr() if n else None,
+                        s.t.data_ptr() if n else None, n, s.t_ref, s.width, s.height)
+    return arr
+
+
+class Plan:
+    """A batch captured into a CUDA graph (veckm_plan_create); launch() replays it."""
+
+    def __init__(self, enc, slices, out, predict: bool):
+        self._keep = (slices, out)
+        arr = _slice_array(slices)
+        h = C.c_void_p()
+        _check(lib().veckm_plan_create(enc.handle, arr, len(slices),
+                                       C.c_void_p(out.data_ptr()) if out.numel() else None,
+                                       1 if predict else 0, C.byref(h)))
+        self._h = h
+        self.out = out
+
+    def launch(self, stream=None):
+        _check(lib().veckm_plan_launch(self._h, Encoder._stream(stream)))
+        return self.out
+
+    @property
+    def kernel_count(self) -> int:
+        return int(lib().veckm_plan_kernel_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().veckm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass
@@ -246,3 +335,41 @@ class Encoder:
 
     def last_launch_count(self) -> int:
         return int(lib().veckm_last_launch_count(self._h))
+
+    def predict_batch(self, slices, out=None, stream=None):
+        """Flows [sum n, 2] of every event of every slice (slice order)."""
+        import torch
+        N = sum(s.n for s in slices)
+        if out is None:
+            out = torch.empty((N, 2), dtype=torch.float32, device="cuda")
+        arr = _slice_array(slices)
+        _check(lib().veckm_predict_batch(self._h, arr, len(slices),
+                                         C.c_void_p(out.data_ptr()) if N else None,
+                                         self._stream(stream)))
+        return out
+
+    def encode_batch(self, slices, out=None, stream=None):
+        """Encodings [sum n, 2D] of every event of every slice (slice order)."""
+        import torch
+        N = sum(s.n for s in slices)
+        if out is None:
+            out = torch.empty((N, 2 * self.p.D), dtype=torch.float32, device="cuda")
+        arr = _slice_array(slices)
+        _check(lib().veckm_encode_batch(self._h, arr, len(slices),
+                                        C.c_void_p(out.data_ptr()) if N else None,
+                                        self._stream(stream)))
+        return out
+
+    def plan(self, slices, out=None, predict: bool = True) -> Plan:
+        import torch
+        N = sum(s.n for s in slices)
+        if out is None:
+            out = torch.empty((N, 2 if predict else 2 * self.p.D), dtype=torch.float32,
+                              device="cuda")
+        return Plan(self, slices, out, predict)
+
+    def autotune(self, width: int, height: int, stream=None):
+        """Pooling launch shapes chosen for width x height: (rows seg, rows warps, cols seg, cols warps)."""
+        t = np.zeros(4, np.int32)
+        _check(lib().veckm_autotune(self._h, width, height, self._stream(stream), _np_ptr(t)))
+        return tuple(int(v) for v in t)
