@@ -249,6 +249,72 @@ void veckm_plan_destroy(veckm_plan *plan);
 veckm_status veckm_autotune(veckm_ctx *ctx, int32_t width, int32_t height, void *stream,
                             int32_t *tuned);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop for event packets from many sensors.  Each packet is one
+ * slice (its events, its sensor size and its start).  veckm_server_submit
+ * admits a packet if its events (8 bytes each, in three 256-byte aligned
+ * arrays) fit in the server's device arena, a ring sized
+ * from free HBM at creation, and refuses it with VECKM_EBUSY otherwise; an
+ * admitted packet's events are copied host-to-device at once on an upload
+ * stream.  A native worker thread takes admitted packets in arrival order,
+ * as many as fit one canvas batch, runs them as one veckm_predict_batch on
+ * its compute stream (at most two batches in flight), copies each packet's
+ * flows to its host buffer and reports the packet complete, with its latency
+ * from submission to completion.  The paper has no serving layer. */
+typedef struct veckm_server veckm_server;
+
+typedef struct {
+    veckm_config model;        /* as for veckm_create; width x height is the canvas */
+    int64_t arena_bytes;       /* device bytes for packets in flight; 0: a quarter of the
+                                  free HBM left after the context is created */
+    int32_t max_batch_packets; /* packets per batch; 0: 256 */
+    int64_t max_batch_events;  /* events per batch; 0: 2^24 */
+    int32_t batch_window_us;   /* a batch that is not full waits for more packets until
+                                  its oldest packet is this old; 0: launch at once */
+} veckm_server_config;
+
+typedef struct {
+    int32_t stream_id;          /* the sensor stream, 0 .. 65535 */
+    uint64_t tag;               /* returned with the completion */
+    const int16_t *h_x, *h_y;   /* host; pinned memory makes the upload asynchronous */
+    const uint32_t *h_t;
+    int64_t n;                  /* 1 .. VECKM_MAX_EVENTS */
+    uint32_t t_ref_us;
+    int32_t width, height;      /* the packet's sensor, at most the canvas */
+    float *h_flow;              /* host [n][2]; written before the completion is reported */
+} veckm_packet;
+
+typedef struct {
+    uint64_t tag;
+    int32_t stream_id;
+    veckm_status status;        /* VECKM_ERANGE if an event of the batch was out of range */
+    int64_t n;
+    double latency_ms;          /* submission to completion, host steady clock */
+    int32_t batch_packets;      /* packets in the batch that carried this one */
+} veckm_completion;
+
+typedef struct {
+    int64_t submitted, admitted, refused, completed, batches, events_completed, streams;
+    double p50_ms, p99_ms, max_ms;  /* latency over completed packets */
+    double wall_s;                  /* first submission to last completion */
+    double gpu_busy_s;              /* sum of batch device times (CUDA events) */
+} veckm_server_stats;
+
+/* Create the server, its context (cfg->model) and its worker thread.  The
+ * host buffers of a packet must stay valid until its completion is polled. */
+veckm_status veckm_server_create(const veckm_server_config *cfg, veckm_server **out);
+/* Admit (VECKM_OK) or refuse (VECKM_EBUSY: no room in the arena) one packet.
+ * VECKM_EINVAL for a malformed packet.  Thread safe. */
+veckm_status veckm_server_submit(veckm_server *srv, const veckm_packet *pkt);
+/* Up to max completions, oldest first; waits up to wait_ms for the first.
+ * Returns how many were written (or a negative status). */
+int32_t veckm_server_poll(veckm_server *srv, veckm_completion *out, int32_t max, int32_t wait_ms);
+/* Wait until every admitted packet has completed (completions stay pollable). */
+veckm_status veckm_server_drain(veckm_server *srv);
+veckm_status veckm_server_get_stats(veckm_server *srv, veckm_server_stats *st);
+/* Stops the worker after the packets in flight and frees everything. */
+void veckm_server_destroy(veckm_server *srv);
+
 /* SplitMix64 + Box-Muller standard normals (the generator behind freq_seed):
  * writes count normals of stream `seed` to h_out.  Host only. */
 void veckm_normals(uint64_t seed, int64_t count, double *h_out);

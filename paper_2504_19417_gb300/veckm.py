@@ -42,6 +42,28 @@ class _Config(C.Structure):
                 ("h_W2", C.c_void_p), ("h_b2", C.c_void_p), ("flags", C.c_uint32)]
 
 
+class _ServerConfig(C.Structure):
+    _fields_ = [("model", _Config), ("arena_bytes", C.c_int64), ("max_batch_packets", C.c_int32),
+                ("max_batch_events", C.c_int64), ("batch_window_us", C.c_int32)]
+
+
+class _Packet(C.Structure):
+    _fields_ = [("stream_id", C.c_int32), ("tag", C.c_uint64), ("h_x", C.c_void_p),
+                ("h_y", C.c_void_p), ("h_t", C.c_void_p), ("n", C.c_int64), ("t_ref_us", C.c_uint32),
+                ("width", C.c_int32), ("height", C.c_int32), ("h_flow", C.c_void_p)]
+
+
+class _Completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("stream_id", C.c_int32), ("status", C.c_int),
+                ("n", C.c_int64), ("latency_ms", C.c_double), ("batch_packets", C.c_int32)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "admitted", "refused", "completed", "batches",
+                                         "events_completed", "streams")] + \
+               [(k, C.c_double) for k in ("p50_ms", "p99_ms", "max_ms", "wall_s", "gpu_busy_s")]
+
+
 class _Slice(C.Structure):
     _fields_ = [("d_x", C.c_void_p), ("d_y", C.c_void_p), ("d_t", C.c_void_p), ("n", C.c_int64),
                 ("t_ref_us", C.c_uint32), ("width", C.c_int32), ("height", C.c_int32)]
@@ -52,7 +74,9 @@ EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noallo
            "veckm_get_frequencies", "veckm_set_timing", "veckm_stage_times",
            "veckm_last_launch_count", "veckm_canvas_layout", "veckm_predict_batch",
            "veckm_encode_batch", "veckm_plan_create", "veckm_plan_launch",
-           "veckm_plan_kernel_count", "veckm_plan_destroy", "veckm_autotune", "veckm_normals")
+           "veckm_plan_kernel_count", "veckm_plan_destroy", "veckm_autotune",
+           "veckm_server_create", "veckm_server_submit", "veckm_server_poll", "veckm_server_drain",
+           "veckm_server_get_stats", "veckm_server_destroy", "veckm_normals")
 
 
 def library_path() -> str:
@@ -92,12 +116,20 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_plan_destroy.argtypes = [P]
     lib.veckm_plan_destroy.restype = None
     lib.veckm_autotune.argtypes = [P, i32, i32, P, P]
+    lib.veckm_server_create.argtypes = [C.POINTER(_ServerConfig), C.POINTER(C.c_void_p)]
+    lib.veckm_server_submit.argtypes = [P, C.POINTER(_Packet)]
+    lib.veckm_server_poll.argtypes = [P, P, i32, i32]
+    lib.veckm_server_drain.argtypes = [P]
+    lib.veckm_server_get_stats.argtypes = [P, C.POINTER(_ServerStats)]
+    lib.veckm_server_destroy.argtypes = [P]
+    lib.veckm_server_destroy.restype = None
     for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
                  "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
                  "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count",
                  "veckm_canvas_layout", "veckm_predict_batch", "veckm_encode_batch",
                  "veckm_plan_create", "veckm_plan_launch", "veckm_plan_kernel_count",
-                 "veckm_autotune"):
+                 "veckm_autotune", "veckm_server_create", "veckm_server_submit",
+                 "veckm_server_poll", "veckm_server_drain", "veckm_server_get_stats"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -210,28 +242,111 @@ class Params:
     freq_seed: int = 0
 
 
+def _make_config(p: Params, W1, b1, W2, b2, T, X, Y, flags: int, keep: list) -> _Config:
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    cfg = _Config(width=p.width, height=p.height, D=p.D, dx=p.dx, dy=p.dy, hidden=p.hidden,
+                  dt_us=p.dt_us, t_span_us=p.t_span_us, sigma2=p.sigma2,
+                  freq_seed=p.freq_seed, flags=flags)
+    for name, a, dt in (("h_T", T, np.float64), ("h_X", X, np.float64),
+                        ("h_Y", Y, np.float64), ("h_W1", W1, np.float32),
+                        ("h_b1", b1, np.float32), ("h_W2", W2, np.float32),
+                        ("h_b2", b2, np.float32)):
+        setattr(cfg, name, _np_ptr(arr(a, dt)))
+    return cfg
+
+
+def _host_ptr(a):
+    """Address of a host buffer: a numpy array or a CPU torch tensor (pinned or not)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert not a.is_cuda and a.is_contiguous()
+    return a.data_ptr()
+
+
+class Server:
+    """The native request loop (veckm_server_*): packets in, flows out.
+
+    ``submit`` admits a packet (returns True) or refuses it when the device
+    arena has no room (returns False).  Host buffers are kept referenced here
+    until the packet's completion has been polled."""
+
+    def __init__(self, p: Params, W1, b1, W2, b2, T=None, X=None, Y=None,
+                 mlp_mode: int = MLP_FP32, arena_bytes: int = 0, max_batch_packets: int = 0,
+                 max_batch_events: int = 0, batch_window_us: int = 0):
+        keep = []
+        cfg = _ServerConfig(model=_make_config(p, W1, b1, W2, b2, T, X, Y, mlp_mode, keep),
+                            arena_bytes=arena_bytes, max_batch_packets=max_batch_packets,
+                            max_batch_events=max_batch_events, batch_window_us=batch_window_us)
+        h = C.c_void_p()
+        _check(lib().veckm_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self.p = p
+        self._bufs = {}
+        self._next_tag = 1
+
+    def submit(self, stream_id: int, x, y, t, t_ref: int, width: int, height: int, out,
+               tag: Optional[int] = None) -> bool:
+        if tag is None:
+            tag = self._next_tag
+            self._next_tag += 1
+        n = int(x.shape[0])
+        pk = _Packet(stream_id, tag, _host_ptr(x), _host_ptr(y), _host_ptr(t), n, t_ref, width,
+                     height, _host_ptr(out))
+        st = lib().veckm_server_submit(self._h, C.byref(pk))
+        if st == VECKM_EBUSY:
+            return False
+        _check(st)
+        self._bufs[tag] = (x, y, t, out)
+        return True
+
+    def poll(self, max_items: int = 1024, wait_ms: int = 0):
+        arr = (_Completion * max_items)()
+        k = lib().veckm_server_poll(self._h, arr, max_items, wait_ms)
+        if k < 0:
+            _check(k)
+        out = []
+        for i in range(k):
+            c = arr[i]
+            self._bufs.pop(c.tag, None)
+            out.append({"tag": c.tag, "stream_id": c.stream_id, "status": c.status, "n": c.n,
+                        "latency_ms": c.latency_ms, "batch_packets": c.batch_packets})
+        return out
+
+    def drain(self):
+        _check(lib().veckm_server_drain(self._h))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().veckm_server_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().veckm_server_destroy(self._h)
+            self._h = None
+            self._bufs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Encoder:
     """One veckm context: tables, weights and per-pixel accumulators on the GPU."""
 
     def __init__(self, p: Params, W1, b1, W2, b2, T=None, X=None, Y=None, mlp_mode: int = MLP_FP32):
         self.p = p
         keep = []
-
-        def arr(a, dt):
-            if a is None:
-                return None
-            a = np.ascontiguousarray(a, dtype=dt)
-            keep.append(a)
-            return a
-
-        cfg = _Config(width=p.width, height=p.height, D=p.D, dx=p.dx, dy=p.dy, hidden=p.hidden,
-                      dt_us=p.dt_us, t_span_us=p.t_span_us, sigma2=p.sigma2,
-                      freq_seed=p.freq_seed, flags=mlp_mode)
-        for name, a, dt in (("h_T", T, np.float64), ("h_X", X, np.float64),
-                            ("h_Y", Y, np.float64), ("h_W1", W1, np.float32),
-                            ("h_b1", b1, np.float32), ("h_W2", W2, np.float32),
-                            ("h_b2", b2, np.float32)):
-            setattr(cfg, name, _np_ptr(arr(a, dt)))
+        cfg = _make_config(p, W1, b1, W2, b2, T, X, Y, mlp_mode, keep)
         h = C.c_void_p()
         _check(lib().veckm_create(C.byref(h), C.byref(cfg)))
         self._h = h
