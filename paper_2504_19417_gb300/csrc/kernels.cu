@@ -733,7 +733,7 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
   const int64_t warps = (n + kPixRecs - 1) / kPixRecs;
   const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
   k_pixsum<DV><<<grid, 256, 0, s>>>(g, tb, nsorted, rec, rpix, acc);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 // Largest dynamic shared memory a box-pass block may ask for.
@@ -757,7 +757,7 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   const int64_t warps = (int64_t)nlines * nseg;
   const int grid = (int)((warps + wpb - 1) / wpb);
   k_box_pass<DV, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, ncnt);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <int DV>
@@ -766,7 +766,7 @@ int gather_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &
                 cudaStream_t s) {
   const int grid = (int)std::min<int64_t>((nK + 7) / 8, (int64_t)num_sms() * 8);
   k_gather_emb<DV><<<grid, 256, 0, s>>>(ev, K, nK, g, tb, pooled, ncnt, emb, err);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <int DV>
@@ -783,7 +783,7 @@ int predict_fp32_impl(const Events &ev, const int64_t *K, int64_t nK, const int2
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * std::max(1, per_sm));
   k_predict_fp32<DV><<<grid, 256, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt,
                                            mlp, flow, err);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace
@@ -830,7 +830,7 @@ int launch_hist(const Events &ev, const Geometry &g, int *cnt, int *err, float *
   if (ev.n == 0) return 0;
   const int grid = (int)std::min<int64_t>((ev.n + 1023) / 1024, (int64_t)num_sms() * 8);
   k_hist<<<grid, 256, 0, s>>>(ev, g, cnt, err, zero_flow);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int scan_blocks(int64_t P) { return (int)((P + kScanBlock - 1) / kScanBlock); }
@@ -842,7 +842,7 @@ int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur
   k_scan_reduce<<<nb, kScanThreads, 0, s>>>(cnt, P, bsum);
   k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb, total);
   k_scan_apply<<<nb, kScanThreads, 0, s>>>(cnt, P, bsum, off, cur);
-  return cudaGetLastError() == cudaSuccess ? 3 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
 }
 
 int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
@@ -851,7 +851,7 @@ int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *
   const int grid = (int)std::min<int64_t>((ev.n + 256 * kPlaceILP - 1) / (256 * kPlaceILP),
                                           (int64_t)num_sms() * 8);
   k_place<<<grid, 256, 0, s>>>(ev, g, cur, rec, pix);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
@@ -883,7 +883,7 @@ int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cu
   const int grid = (int)((P + 255) / 256);
   k_count_rows<<<grid, 256, 0, s>>>(cnt, cnt_tmp, g.W, g.H, g.dx);
   k_count_cols<<<grid, 256, 0, s>>>(cnt_tmp, ncnt, g.W, g.H, g.dy);
-  return cudaGetLastError() == cudaSuccess ? 2 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,

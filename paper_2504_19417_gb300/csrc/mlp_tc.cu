@@ -100,15 +100,19 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fp16) {
   return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Waits for the phase with the given parity.  try_wait suspends the thread
+// in hardware until the phase completes or the hint (ns) runs out, so a
+// waiting warp takes no issue slots from the warps doing the work; the loop
+// gives up after kWaitLimitCycles.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000000u)
         : "memory");
     if (ok) return true;
     if (clock64() - t0 > kWaitLimitCycles) return false;
@@ -524,7 +528,7 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm);
   kern<<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
                                   err);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace
