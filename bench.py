@@ -154,12 +154,42 @@ def mlp_flops(nK, D, hidden=128):
 
 
 def _dist():
+    """(module, rank, world size, local rank); one process per GPU under
+    torchrun.  VECKM_DIST_BACKEND selects the backend (nccl by default; the
+    CPU tests use gloo)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(os.environ.get("VECKM_DIST_BACKEND", "nccl"))
         return dist, int(os.environ["RANK"]), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
+
+
+def max_over_ranks(dist, x: float) -> float:
+    """The largest x over all ranks (the job takes as long as its slowest rank)."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_slice_def(workload: str, rank: int, scale: float = 1.0) -> dict:
+    """The generator arguments of this rank's slice: the workload's shape with
+    a seed of its own (weak scaling: every rank encodes an independent slice)."""
+    from paper_2504_19417_gb300 import synth
+    w = dict(synth.WORKLOADS[workload])
+    w["seed"] = w["seed"] + 100 * rank
+    w["n"] = max(1, int(round(w["n"] * scale)))
+    return w
+
+
+def job_rate(ws: int, units_per_rank: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the max time."""
+    return ws * units_per_rank * steps / (total_ms / 1000.0)
 
 
 def run_reference(args):
@@ -209,9 +239,7 @@ def run_ours(args):
     modes = {"bf16": vk.MLP_BF16, "fp16": vk.MLP_FP16, "fp32": vk.MLP_FP32,
              "fp16-acc16": vk.MLP_FP16 | vk.ACC_FP16, "bf16-acc16": vk.MLP_BF16 | vk.ACC_FP16}
     mode = modes[args.mode]
-    w_def = dict(synth.WORKLOADS[args.workload])
-    w_def["seed"] = w_def["seed"] + 100 * rank  # each rank its own independent slice
-    w_def["n"] = max(1, int(round(w_def["n"] * args.scale)))
+    w_def = rank_slice_def(args.workload, rank, args.scale)
     D = w_def.pop("D")
     sl = synth.event_slice(**w_def)
     T, X, Y = synth.frequencies(D, 0)
@@ -248,11 +276,7 @@ def run_ours(args):
             dist.barrier()
         wall = time.perf_counter() - t0
         per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(nsteps)])
-        total_ms = float(evs[0].elapsed_time(evs[-1]))
-        if dist:
-            tt = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total_ms = float(tt.item())
+        total_ms = max_over_ranks(dist, float(evs[0].elapsed_time(evs[-1])))
         return total_ms, per, wall
 
     clocks = ClockSampler(local)
@@ -265,7 +289,7 @@ def run_ours(args):
     enc.set_timing(False)
     clk = clocks.stop() if not args.lean else None
     enc.sync_status()
-    value = ws * nK * args.steps / (total_ms / 1000.0)
+    value = job_rate(ws, nK, args.steps, total_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -345,11 +369,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(ne):
         enc.predict_host(hx, hy, ht, sl.t_ref, out=hflow, stream=stream)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
     out["e2e"] = {"value": ws * nK * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sl.n * 8,
                   "d2h_bytes_per_step": nK * 8, "ms_per_step": 1000 * e2e_s / ne}
 
