@@ -248,6 +248,7 @@ def run_ours(args):
     p = vk.Params(width=sl.width, height=sl.height, D=D, dx=10, dy=10, dt_us=16_000,
                   t_span_us=span)
     enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=mode)
+    tuned = enc.autotune(sl.width, sl.height) if not args.no_autotune else None
     x = torch.from_numpy(sl.x).cuda()
     y = torch.from_numpy(sl.y).cuda()
     t = torch.from_numpy(sl.t.view(np.int32)).cuda()
@@ -302,6 +303,9 @@ def run_ours(args):
                    "events_per_slice": sl.n, "flows_per_step": nK, "D": D, "window": "21x21",
                    "dt_us": 16_000, "mlp": f"{2 * D}->128->2 ReLU", "mlp_precision": args.mode,
                    "parallelism": f"replicas x{ws}, one slice per GPU",
+                   "pooling_shapes": ({"rows_seg": tuned[0], "rows_warps": tuned[1],
+                                       "cols_seg": tuned[2], "cols_warps": tuned[3]}
+                                      if tuned else "default"),
                    "l2": "inputs larger than L2 (each step writes 2 x accumulator grid)"},
         "gpu_launches": int(launches_per_step * args.steps),
     }
@@ -401,6 +405,11 @@ def run_ours(args):
             "flow_rel_max": float(f_err.max()), "flow_rel_mean": float(f_err.mean()),
             "flow_abs_max": float(f_abs.max()), "flow_abs_mean": float(f_abs.mean()),
             "flow_rel_floor": "0.25 x median |flow|"}
+    if rank == 0 and not args.no_recipes:
+        try:
+            out["recipes"] = recipes_leg(args, mode, stream)
+        except Exception as e:  # the headline line is printed regardless
+            out["recipes"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_batch:
         try:
             out["batch"] = batch_leg(args, mode, stream)
@@ -413,6 +422,46 @@ def run_ours(args):
             out["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def recipes_leg(args, mode, stream):
+    """The paper's four parameter recipes (window radii 8/10, delta_t 16/12 ms,
+    640x480, D = 64) on the 640x480 2M-event slice, each with its pooling
+    shapes autotuned for its window; flows/s per recipe."""
+    import torch
+    from paper_2504_19417_gb300 import synth
+    from paper_2504_19417_gb300 import veckm as vk
+    sl, _ = synth.workload("slice-640x480-2M")
+    x = torch.from_numpy(sl.x).cuda()
+    y = torch.from_numpy(sl.y).cuda()
+    t = torch.from_numpy(sl.t.view(np.int32)).cuda()
+    flow = torch.empty((sl.n, 2), dtype=torch.float32, device="cuda")
+    out = {}
+    for name, r in sorted(synth.RECIPES.items()):
+        T, X, Y = synth.frequencies(r["D"], 0)
+        w = synth.mlp_weights(r["D"], 128, 3)
+        p = vk.Params(width=r["width"], height=r["height"], D=r["D"], dx=r["dx"], dy=r["dy"],
+                      dt_us=r["dt_us"], t_span_us=int(sl.t.max()) - sl.t_ref)
+        enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=mode)
+        tuned = enc.autotune(r["width"], r["height"], stream)
+        for _ in range(args.warmup):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k = max(3, args.steps // 2)
+        a.record(stream)
+        for _ in range(k):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / k
+        enc.sync_status()
+        out[name] = {"value": sl.n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "window": f"{2 * r['dx'] + 1}x{2 * r['dy'] + 1}", "dt_us": r["dt_us"],
+                     "tuned_pooling": {"rows_seg": tuned[0], "rows_warps": tuned[1],
+                                       "cols_seg": tuned[2], "cols_warps": tuned[3]}}
+        enc.close()
+    return out
 
 
 def batch_leg(args, mode, stream):
@@ -603,6 +652,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-slice batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-recipes", action="store_true", help="skip the parameter-recipe leg")
+    ap.add_argument("--no-autotune", action="store_true", help="default pooling launch shapes")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--batch-scale", type=float, default=1.0, help="events x scale of the batch leg")
     args = ap.parse_args()

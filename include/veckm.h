@@ -177,6 +177,22 @@ veckm_status veckm_stage_times(veckm_ctx *ctx, double *ms, int64_t *calls, int n
 /* Number of kernel launches the last encode/predict call made. */
 int veckm_last_launch_count(const veckm_ctx *ctx);
 
+/* Kernel density read back from encodings (Lemma 1 of Section 2.2.1), the
+ * "general-purpose encoder" use of an encoding.  For query i, with e the row
+ * d_row[i] of d_emb (float [nrows][2D], as veckm_encode writes it) and the
+ * integer offset q = (d_qt[i] microseconds, d_qx[i], d_qy[i] pixels) from
+ * that row's event:
+ *   d_out[i] = (1/D) sum_d [Re e_d cos a_d + Im e_d sin a_d],
+ *   a_d = qt T_d / dt + qx X_d / dx + qy Y_d / dy,
+ * i.e. Re((1/D) sum_d e_d conj(exp(i a_d))), which approaches the Gaussian
+ * kernel density of the event's window at q as D grows.  Every term of a_d is
+ * reduced modulo one turn exactly (64-bit fixed point), whatever the offset.
+ * A row outside [0, nrows) gives 0 and sets the device error word
+ * (VECKM_ERANGE at the next status check).  Device buffers; nq may be 0. */
+veckm_status veckm_kde_query(veckm_ctx *ctx, const float *d_emb, int64_t nrows,
+                             const int64_t *d_row, const int32_t *d_qt, const int32_t *d_qx,
+                             const int32_t *d_qy, int64_t nq, float *d_out, void *stream);
+
 /* ------------------------------------------------------------------ batches
  * Several slices, possibly from sensors of different sizes, encoded in one
  * pass.  The library lays the sensors out on a canvas, one large virtual

@@ -22,6 +22,7 @@ struct veckm_ctx {
   // device state
   float4 *tx = nullptr, *ty = nullptr, *sx = nullptr, *sy = nullptr;
   uint2 *wt = nullptr;
+  uint2 *wxy = nullptr;  // X then Y frequencies in 64-bit fixed-point turns per pixel
   float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
   uint16_t *W1h = nullptr;
   float4 *acc = nullptr, *hbuf = nullptr;

@@ -104,7 +104,7 @@ void free_all(veckm_ctx *c) {
   void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
                   c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
                   c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->cx, c->cy, c->ct,
-                  c->slice_tab};
+                  c->slice_tab, c->wxy};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -333,16 +333,22 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   std::vector<float> hty = phase_rows(c->Y, wy, 0, g.H, 1);
   std::vector<float> hsx = phase_rows(c->X, wx, 1, 1, 1);
   std::vector<float> hsy = phase_rows(c->Y, wy, 1, 1, 1);
-  // temporal frequencies in turns per microsecond, reduced to [-1/2, 1/2],
-  // as 64-bit fixed point (the device reduces t * w mod 1 exactly)
-  std::vector<uint2> hwt(D);
-  for (int d = 0; d < D; ++d) {
-    const double w = c->T[d] * wt / (2.0 * 3.14159265358979323846);
+  // frequencies in turns per unit (microsecond, pixel), reduced to
+  // [-1/2, 1/2], as 64-bit fixed point (the device reduces q * w mod 1
+  // exactly for an integer q)
+  auto fixed_turns = [](double freq_per_unit) {
+    const double w = freq_per_unit / (2.0 * 3.14159265358979323846);
     const double r = w - std::nearbyint(w);
     const double q = std::ldexp(r, 64);
     const int64_t qi = q >= 9.2233720368547758e18 ? INT64_MAX : (int64_t)std::llround(q);
     const uint64_t u = (uint64_t)qi;
-    hwt[d] = make_uint2((uint32_t)(u & 0xffffffffu), (uint32_t)(u >> 32));
+    return make_uint2((uint32_t)(u & 0xffffffffu), (uint32_t)(u >> 32));
+  };
+  std::vector<uint2> hwt(D), hwxy(2 * (size_t)D);
+  for (int d = 0; d < D; ++d) {
+    hwt[d] = fixed_turns(c->T[d] * wt);
+    hwxy[d] = fixed_turns(c->X[d] * wx);
+    hwxy[D + d] = fixed_turns(c->Y[d] * wy);
   }
   const int IN = 2 * D;
   c->hW1.assign(cfg->h_W1, cfg->h_W1 + (size_t)c->hidden * IN);
@@ -362,6 +368,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(dalloc(&c->sy, (size_t)g.U));
   VK_TRY(dalloc(&c->ty, (size_t)g.H * g.U));
   VK_TRY(dalloc(&c->wt, (size_t)D));
+  VK_TRY(dalloc(&c->wxy, 2 * (size_t)D));
   VK_TRY(dalloc(&c->W1, (size_t)c->hidden * IN));
   VK_TRY(dalloc(&c->W1t, (size_t)c->hidden * IN));
   VK_TRY(dalloc(&c->W1h, (size_t)c->hidden * IN));
@@ -384,6 +391,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(cudaMemcpy(c->sx, hsx.data(), hsx.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->sy, hsy.data(), hsy.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->wt, hwt.data(), hwt.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->wxy, hwxy.data(), hwxy.size() * sizeof(uint2), cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1, c->hW1.data(), c->hW1.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1t, hW1t.data(), hW1t.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1h, hW1h.data(), hW1h.size() * 2, cudaMemcpyHostToDevice));

@@ -253,6 +253,17 @@ WORKLOADS = {
 }
 
 
+# The parameter recipes of the paper's recipe table (Section 2.3): the
+# 640x480 sensor, D = 64, window radii 8 or 10 pixels, delta_t 16 or 12 ms
+# (slices of 2 delta_t).
+RECIPES = {
+    "640x480_32ms_C64_k8": dict(width=640, height=480, D=64, dx=8, dy=8, dt_us=16_000),
+    "640x480_32ms_C64_k10": dict(width=640, height=480, D=64, dx=10, dy=10, dt_us=16_000),
+    "640x480_24ms_C64_k8": dict(width=640, height=480, D=64, dx=8, dy=8, dt_us=12_000),
+    "640x480_24ms_C64_k10": dict(width=640, height=480, D=64, dx=10, dy=10, dt_us=12_000),
+}
+
+
 def workload(name: str, scale: float = 1.0) -> tuple[EventSlice, int]:
     """The named slice (optionally with ``scale`` times the events) and its D."""
     w = dict(WORKLOADS[name])

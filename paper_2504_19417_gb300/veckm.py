@@ -76,7 +76,7 @@ EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noallo
            "veckm_encode_batch", "veckm_plan_create", "veckm_plan_launch",
            "veckm_plan_kernel_count", "veckm_plan_destroy", "veckm_autotune",
            "veckm_server_create", "veckm_server_submit", "veckm_server_poll", "veckm_server_drain",
-           "veckm_server_get_stats", "veckm_server_destroy", "veckm_normals")
+           "veckm_server_get_stats", "veckm_server_destroy", "veckm_kde_query", "veckm_normals")
 
 
 def library_path() -> str:
@@ -123,13 +123,15 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_server_get_stats.argtypes = [P, C.POINTER(_ServerStats)]
     lib.veckm_server_destroy.argtypes = [P]
     lib.veckm_server_destroy.restype = None
+    lib.veckm_kde_query.argtypes = [P, P, i64, P, P, P, P, i64, P, P]
     for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
                  "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
                  "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count",
                  "veckm_canvas_layout", "veckm_predict_batch", "veckm_encode_batch",
                  "veckm_plan_create", "veckm_plan_launch", "veckm_plan_kernel_count",
                  "veckm_autotune", "veckm_server_create", "veckm_server_submit",
-                 "veckm_server_poll", "veckm_server_drain", "veckm_server_get_stats"):
+                 "veckm_server_poll", "veckm_server_drain", "veckm_server_get_stats",
+                 "veckm_kde_query"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -482,6 +484,18 @@ class Encoder:
             out = torch.empty((N, 2 if predict else 2 * self.p.D), dtype=torch.float32,
                               device="cuda")
         return Plan(self, slices, out, predict)
+
+    def kde_query(self, emb, rows, qt, qx, qy, out=None, stream=None):
+        """Lemma 1 read-back at integer offsets (qt us, qx, qy px) from the events of emb rows."""
+        import torch
+        nq = rows.numel()
+        if out is None:
+            out = torch.empty(nq, dtype=torch.float32, device=emb.device)
+        _check(lib().veckm_kde_query(self._h, self._dev(emb, torch.float32), emb.shape[0],
+                                     self._dev(rows, torch.int64), self._dev(qt, torch.int32),
+                                     self._dev(qx, torch.int32), self._dev(qy, torch.int32), nq,
+                                     self._dev(out, torch.float32), self._stream(stream)))
+        return out
 
     def autotune(self, width: int, height: int, stream=None):
         """Pooling launch shapes chosen for width x height: (rows seg, rows warps, cols seg, cols warps)."""

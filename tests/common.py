@@ -41,7 +41,10 @@ def emb_rel_err(gpu, ref):
     return num / den
 
 
-UNIT_ROUNDOFF = {vk.MLP_BF16: 2.0 ** -8, vk.MLP_FP16: 2.0 ** -11}
+# unit roundoff of the first layer's operands; FP32 (the plain head) uses the
+# same propagation bound with u = 2^-24, where the 1e-5 term (FP32
+# accumulation and encoder error) dominates
+UNIT_ROUNDOFF = {vk.MLP_FP32: 2.0 ** -24, vk.MLP_BF16: 2.0 ** -8, vk.MLP_FP16: 2.0 ** -11}
 
 
 def half_flow_bound(emb_ref, w, mode):
