@@ -405,6 +405,11 @@ def run_ours(args):
             "flow_rel_max": float(f_err.max()), "flow_rel_mean": float(f_err.mean()),
             "flow_abs_max": float(f_abs.max()), "flow_abs_mean": float(f_abs.mean()),
             "flow_rel_floor": "0.25 x median |flow|"}
+    if rank == 0 and not args.no_sparse:
+        try:
+            out["sparse_k"] = sparse_leg(args, mode, stream)
+        except Exception as e:  # the headline line is printed regardless
+            out["sparse_k"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_recipes:
         try:
             out["recipes"] = recipes_leg(args, mode, stream)
@@ -422,6 +427,63 @@ def run_ours(args):
             out["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def sparse_leg(args, mode, stream):
+    """The paper's runtime example (Section 3): 0.5 M events and 10 k requested
+    flows with a 17x17 window (dx = dy = 8), here on the 640x480 slice: the
+    dense pooled form, the direct window form and the runtime-model choice.
+    Also the model's coefficients measured on this run (ns)."""
+    import torch
+    from paper_2504_19417_gb300 import synth
+    from paper_2504_19417_gb300 import veckm as vk
+    sl, D = synth.workload("slice-640x480-2M", scale=0.25)
+    r = synth.RECIPES["640x480_32ms_C64_k8"]
+    T, X, Y = synth.frequencies(D, 0)
+    w = synth.mlp_weights(D, 128, 3)
+    p = vk.Params(width=sl.width, height=sl.height, D=D, dx=r["dx"], dy=r["dy"], dt_us=r["dt_us"],
+                  t_span_us=int(sl.t.max()) - sl.t_ref)
+    enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=mode)
+    enc.autotune(sl.width, sl.height, stream)
+    x = torch.from_numpy(sl.x).cuda()
+    y = torch.from_numpy(sl.y).cuda()
+    t = torch.from_numpy(sl.t.view(np.int32)).cuda()
+    rng = np.random.default_rng(9)
+    nK = 10_000
+    K = torch.from_numpy(np.sort(rng.choice(sl.n, nK, replace=False)).astype(np.int64)).cuda()
+    flow = torch.empty((nK, 2), dtype=torch.float32, device="cuda")
+    res = {"workload": f"640x480, {sl.n} events, {nK} requested flows, 17x17 window"}
+    stages = {}
+    for name, path in (("dense", vk.PATH_DENSE), ("direct", vk.PATH_DIRECT), ("auto", vk.PATH_AUTO)):
+        enc.set_path(path)
+        for _ in range(args.warmup):
+            enc.predict(x, y, t, sl.t_ref, K=K, out=flow, stream=stream)
+        enc.set_timing(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k = max(3, args.steps // 2)
+        a.record(stream)
+        for _ in range(k):
+            enc.predict(x, y, t, sl.t_ref, K=K, out=flow, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / k
+        st, calls = enc.stage_times()
+        enc.set_timing(False)
+        stages[name] = {s_: 1000 * v / max(1, calls[s_]) for s_, v in st.items()}
+        res[name] = {"ms_per_call": ms, "flows_per_s": nK / (ms * 1e-3),
+                     "path": {1: "dense", 2: "direct"}[enc.last_path()],
+                     "stage_us": {k_: round(v, 1) for k_, v in stages[name].items()}}
+    enc.sync_status()
+    P = sl.width * sl.height
+    area = (2 * r["dx"] + 1) * (2 * r["dy"] + 1)
+    dense_px_us = sum(stages["dense"][s_] for s_ in ("pool_rows", "counts", "pool_cols"))
+    res["model_ns"] = {
+        "pixel": 1000 * dense_px_us / P,
+        "flow_dense": 1000 * stages["dense"]["gather"] / nK,
+        "flow_window": 1000 * stages["direct"]["gather"] / (nK * area)}
+    enc.close()
+    return res
 
 
 def recipes_leg(args, mode, stream):
@@ -654,6 +716,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-recipes", action="store_true", help="skip the parameter-recipe leg")
     ap.add_argument("--no-autotune", action="store_true", help="default pooling launch shapes")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-request leg")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--batch-scale", type=float, default=1.0, help="events x scale of the batch leg")
     args = ap.parse_args()

@@ -177,6 +177,28 @@ veckm_status veckm_stage_times(veckm_ctx *ctx, double *ms, int64_t *calls, int n
 /* Number of kernel launches the last encode/predict call made. */
 int veckm_last_launch_count(const veckm_ctx *ctx);
 
+/* Dense pooling or the direct window form.  Algorithm 1 computes each
+ * requested flow by looping over its window (the paper's Lines 11-21, cost C
+ * per flow in Eq. runtime of Section 2.2.2).  The dense form pools every
+ * pixel once with separable box sums (cost per pixel, then little per flow);
+ * the direct form keeps the window loop, visiting only occupied window pixels
+ * (one warp per requested event), and skips the pooling passes and the clear
+ * of the pixel grid.  VECKM_PATH_AUTO (default) picks per call the smaller of
+ *   dense:  k_pixel * W*H + k_flow_dense * nK
+ *   direct: k_flow_window * (2dx+1)(2dy+1) * nK,
+ * with coefficients measured on GB300 (settable).  The direct form's
+ * perceptron is the FP32 one whatever the flags; with D > 128 predictions
+ * stay dense.  Results agree to FP32 rounding. */
+#define VECKM_PATH_AUTO 0
+#define VECKM_PATH_DENSE 1
+#define VECKM_PATH_DIRECT 2
+veckm_status veckm_set_path(veckm_ctx *ctx, int32_t path);
+/* The path the last encode/predict call took (VECKM_PATH_DENSE or _DIRECT). */
+int veckm_last_path(const veckm_ctx *ctx);
+/* The model's coefficients in nanoseconds (all positive; flow_dense may be 0). */
+veckm_status veckm_set_path_model(veckm_ctx *ctx, double pixel_ns, double flow_dense_ns,
+                                  double flow_window_ns);
+
 /* Kernel density read back from encodings (Lemma 1 of Section 2.2.1), the
  * "general-purpose encoder" use of an encoding.  For query i, with e the row
  * d_row[i] of d_emb (float [nrows][2D], as veckm_encode writes it) and the

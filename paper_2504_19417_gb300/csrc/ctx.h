@@ -20,7 +20,7 @@ struct veckm_ctx {
   double sigma2 = 25.0;
   std::vector<double> T, X, Y;
   // device state
-  float4 *tx = nullptr, *ty = nullptr, *sx = nullptr, *sy = nullptr;
+  float4 *tx = nullptr, *ty = nullptr, *sx = nullptr, *sy = nullptr, *rx = nullptr, *ry = nullptr;
   uint2 *wt = nullptr;
   uint2 *wxy = nullptr;  // X then Y frequencies in 64-bit fixed-point turns per pixel
   float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
@@ -61,8 +61,14 @@ struct veckm_ctx {
   size_t slice_tab_cap = 0, h_slice_tab_cap = 0;
   cudaEvent_t tab_copied = nullptr;  // the last copy out of h_slice_tab
   int live_plans = 0;                // captured graphs that use this context's buffers
+  // dense pooling or direct window form (Eq. runtime): seconds per pixel of
+  // the dense passes, per flow of the dense gather, per flow and window pixel
+  // of the direct form, measured on GB300 (0.5 M events, 10 k flows, 640x480,
+  // 17x17 window; settable with veckm_set_path_model)
+  int path = VECKM_PATH_AUTO, last_path = 0;
+  double k_pixel = 0.43e-9, k_flow_dense = 1.53e-9, k_flow_window = 0.077e-9;
 
-  veckm::Tables tables() const { return veckm::Tables{tx, ty, sx, sy, wt}; }
+  veckm::Tables tables() const { return veckm::Tables{tx, ty, sx, sy, wt, rx, ry}; }
   veckm::Tune tune_for(const veckm::Geometry &gg) const {
     for (const TuneEntry &t : tunes)
       if (t.W == gg.W && t.H == gg.H && t.acc16 == (flags & VECKM_ACC_FP16)) return t.tn;

@@ -716,6 +716,231 @@ __global__ void __launch_bounds__(256) k_predict_fp32(Events ev, const int64_t *
 }
 
 // Large dynamic shared memory, and a carveout that lets several CTAs share an SM.
+// ---------------------------------------------------------------------------
+// 8. the direct window form (the per-event window loop of Algorithm 1), for
+// requests that are few next to the sensor's pixels.
+//
+// 8a. per-pixel phase sums written once per occupied pixel: warp c owns the
+// pixels whose first record lies in [c*kPixRecs, (c+1)*kPixRecs) of the
+// pixel-sorted records and sums each to its last record, past the range if
+// need be.  Plain stores only, no clear: pixels without events keep whatever
+// they held, and the direct form never reads them.
+template <int DV>
+__global__ void __launch_bounds__(256) k_pixsum_owned(Tables tb, const int *__restrict__ nsorted,
+                                                      const int2 *__restrict__ rec,
+                                                      const int *__restrict__ rpix,
+                                                      float4 *__restrict__ acc) {
+  constexpr int U = 32 * DV;
+  const int lane = threadIdx.x & 31;
+  const int64_t ns = *nsorted;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  uint2 w[DV][2];
+  load_freqs<DV>(tb.wt, lane, w);
+  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kPixRecs;
+       r0 < ns; r0 += nw * kPixRecs) {
+    const int64_t r1 = r0 + kPixRecs < ns ? r0 + kPixRecs : ns;
+    // the first record of the range that starts a pixel (pixels ascend)
+    int64_t c = r0;
+    if (r0 > 0) {
+      const int prev = __ldg(rpix + r0 - 1);
+      for (;;) {
+        const int64_t i = c + lane;
+        const int pl = i < ns ? __ldg(rpix + i) : -2;
+        const unsigned m = __ballot_sync(kFull, pl != prev);
+        if (m) {
+          c += __ffs(m) - 1;
+          break;
+        }
+        c += 32;
+      }
+      if (c >= r1) continue;  // every record of the range continues an earlier pixel
+    }
+    int sp = -1;
+    float4 s[DV];
+#pragma unroll
+    for (int v = 0; v < DV; ++v) s[v] = f4zero();
+    auto store = [&]() {
+      float4 *dst = acc + (size_t)sp * U + lane;
+#pragma unroll
+      for (int v = 0; v < DV; ++v) dst[32 * v] = s[v];
+    };
+    bool done = false;
+    for (int64_t b = c; !done && b < ns; b += 32) {
+      const int m = (int)(ns - b < 32 ? ns - b : 32);
+      const uint32_t tl = lane < m ? (uint32_t)__ldg(&rec[b + lane].x) : 0u;
+      const int pl = lane < m ? __ldg(rpix + b + lane) : 0;
+      for (int j = 0; j < m; ++j) {
+        const int pj = __shfl_sync(kFull, pl, j);
+        const uint32_t tj = __shfl_sync(kFull, tl, j);
+        if (pj != sp) {
+          if (sp >= 0) store();
+          if (b + j >= r1) {  // this pixel starts past the range: another warp's
+            done = true;
+            sp = -1;
+            break;
+          }
+          sp = pj;
+#pragma unroll
+          for (int v = 0; v < DV; ++v) s[v] = f4zero();
+        }
+#pragma unroll
+        for (int v = 0; v < DV; ++v) s[v] = add4(s[v], time_phase2(tj, w[v][0], w[v][1]));
+      }
+    }
+    if (sp >= 0) store();  // the records ended inside this warp's last pixel
+  }
+}
+
+// 8b. one warp per requested event: emb = conj(phase_t) / n * sum over the
+// window of PixelEmbed[p] exp(i ((x_p - x) X/dx + (y_p - y) Y/dy)), the sum
+// visiting only occupied pixels (a ballot over the counts of each window
+// row), n = the window count.  FLOW: the perceptron follows in the same warp
+// (W1 transposed, b1, W2 in shared memory; lane j computes hidden units
+// j, j+32, j+64, j+96 from the encoding staged in shared memory).
+constexpr int kDirWarps = 8;
+constexpr int kDirBatch = 4;  // occupied window pixels whose loads are in flight together
+
+template <int DV, bool FLOW>
+__global__ void __launch_bounds__(32 * kDirWarps) k_direct(Events ev, const int64_t *__restrict__ K,
+                                                         int64_t nK, Geometry g, Tables tb,
+                                                         const float4 *__restrict__ acc,
+                                                         const int *__restrict__ cnt, MLP mlp,
+                                                         float *__restrict__ out, int *err) {
+  constexpr int U = 32 * DV, IN = 4 * U;
+  extern __shared__ float4 smem4[];
+  float *sW = reinterpret_cast<float *>(smem4);   // FLOW: [IN][128] W1 transposed
+  float *sE = sW + (FLOW ? IN * kHid : 0);        // [warps][IN] encoding rows
+  float *sB1 = sE + kDirWarps * IN;               // [128]
+  float *sW2 = sB1 + kHid;                        // [2][128]
+  if (FLOW) {
+    for (int i = threadIdx.x; i < IN * kHid / 4; i += blockDim.x)
+      reinterpret_cast<float4 *>(sW)[i] = __ldg(reinterpret_cast<const float4 *>(mlp.W1t) + i);
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+      sB1[i] = mlp.b1[i];
+      sW2[i] = mlp.W2[i];
+      sW2[kHid + i] = mlp.W2[kHid + i];
+    }
+    __syncthreads();
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int D = 2 * U;
+  uint2 w[DV][2];
+  load_freqs<DV>(tb.wt, lane, w);
+  const int64_t nwarps = (int64_t)gridDim.x * kDirWarps;
+  for (int64_t i = (int64_t)blockIdx.x * kDirWarps + warp; i < nK; i += nwarps) {
+    int64_t k = i;
+    bool valid = true;
+    if (K) {
+      k = K[i];
+      if (k < 0 || k >= ev.n) {
+        valid = false;
+        if (lane == 0) atomicOr(err, ERR_INDEX_RANGE);
+      }
+    }
+    int x = 0, y = 0;
+    uint32_t trel = 0;
+    if (valid) {
+      x = ev.x[k];
+      y = ev.y[k];
+      valid = event_ok(x, y, ev.t[k], ev, g.W, g.H, trel);
+      if (!valid && lane == 0) atomicOr(err, ERR_EVENT_RANGE);
+    }
+    float4 e[DV];
+#pragma unroll
+    for (int v = 0; v < DV; ++v) e[v] = f4zero();
+    if (valid) {
+      int n = 0;
+      for (int yy = max(0, y - g.dy); yy <= min(g.H - 1, y + g.dy); ++yy) {
+        float4 rp[DV];  // exp(i (yy - y) Y/dy)
+#pragma unroll
+        for (int v = 0; v < DV; ++v) rp[v] = __ldg(tb.ry + (size_t)(yy - y + g.dy) * U + lane + 32 * v);
+        for (int x0 = x - g.dx; x0 <= x + g.dx; x0 += 32) {
+          const int xl = x0 + lane;
+          const int c = (xl <= x + g.dx && xl >= 0 && xl < g.W) ? __ldg(cnt + (size_t)yy * g.W + xl) : 0;
+          n += c;
+          unsigned m = __ballot_sync(kFull, c > 0);
+          // occupied pixels four at a time: every load issued before any use
+          while (m) {
+            int xs[kDirBatch];
+#pragma unroll
+            for (int q = 0; q < kDirBatch; ++q) {
+              xs[q] = m ? x0 + __ffs(m) - 1 : -1;
+              m &= m - 1;
+            }
+            float4 av[kDirBatch][DV], tv[kDirBatch][DV];
+#pragma unroll
+            for (int q = 0; q < kDirBatch; ++q) {
+              const int xj = xs[q] >= 0 ? xs[q] : xs[0];
+              const float4 *a = acc + ((size_t)yy * g.W + xj) * U + lane;
+              const float4 *tr = tb.rx + (size_t)(xj - x + g.dx) * U + lane;  // exp(i (xj - x) X/dx)
+#pragma unroll
+              for (int v = 0; v < DV; ++v) {
+                av[q][v] = __ldg(a + 32 * v);
+                tv[q][v] = __ldg(tr + 32 * v);
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < kDirBatch; ++q) {
+              if (xs[q] < 0) break;
+#pragma unroll
+              for (int v = 0; v < DV; ++v) e[v] = add4(e[v], cmul2(av[q][v], cmul2(tv[q][v], rp[v])));
+            }
+          }
+        }
+      }
+      n = __reduce_add_sync(kFull, n);  // >= 1: the event's own pixel
+      const float inv = 1.0f / (float)n;
+#pragma unroll
+      for (int v = 0; v < DV; ++v) {
+        const float4 o = cmul2c(e[v], time_phase2(trel, w[v][0], w[v][1]));
+        e[v] = make_float4(o.x * inv, o.y * inv, o.z * inv, o.w * inv);
+      }
+    }
+    if (!FLOW) {
+      float *row = out + (size_t)i * 2 * D;
+#pragma unroll
+      for (int v = 0; v < DV; ++v) {
+        const int u = lane + 32 * v;
+        *reinterpret_cast<float2 *>(row + 2 * u) = make_float2(e[v].x, e[v].z);
+        *reinterpret_cast<float2 *>(row + D + 2 * u) = make_float2(e[v].y, e[v].w);
+      }
+    } else {
+      float *se = sE + warp * IN;  // [Re | Im], the perceptron's input order
+#pragma unroll
+      for (int v = 0; v < DV; ++v) {
+        const int u = lane + 32 * v;
+        *reinterpret_cast<float2 *>(se + 2 * u) = make_float2(e[v].x, e[v].z);
+        *reinterpret_cast<float2 *>(se + D + 2 * u) = make_float2(e[v].y, e[v].w);
+      }
+      __syncwarp();
+      float h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[q] = sB1[lane + 32 * q];
+      for (int cI = 0; cI < IN; ++cI) {
+        const float ec = se[cI];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = fmaf(sW[cI * kHid + lane + 32 * q], ec, h[q]);
+      }
+      float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float a = fmaxf(h[q], 0.f);
+        f0 = fmaf(sW2[lane + 32 * q], a, f0);
+        f1 = fmaf(sW2[kHid + lane + 32 * q], a, f1);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        f0 += __shfl_xor_sync(kFull, f0, o);
+        f1 += __shfl_xor_sync(kFull, f1, o);
+      }
+      if (lane == 0)
+        *reinterpret_cast<float2 *>(out + 2 * i) =
+            valid ? make_float2(f0 + mlp.b2[0], f1 + mlp.b2[1]) : make_float2(0.f, 0.f);
+      __syncwarp();
+    }
+  }
+}
+
 template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -757,6 +982,32 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   const int64_t warps = (int64_t)nlines * nseg;
   const int grid = (int)((warps + wpb - 1) / wpb);
   k_box_pass<DV, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, ncnt);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <int DV>
+int pixsum_owned_impl(const Tables &tb, const int *nsorted, const int2 *rec, const int *rpix,
+                      int64_t n, float4 *acc, cudaStream_t s) {
+  if (n == 0) return 0;
+  const int64_t warps = (n + kPixRecs - 1) / kPixRecs;
+  const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
+  k_pixsum_owned<DV><<<grid, 256, 0, s>>>(tb, nsorted, rec, rpix, acc);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <int DV, bool FLOW>
+int direct_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
+                const Tables &tb, const float4 *acc, const int *cnt, const MLP &mlp, float *out,
+                int *err, cudaStream_t s) {
+  if (nK == 0) return 0;
+  constexpr int IN = 128 * DV;
+  const size_t sm = sizeof(float) * ((FLOW ? (size_t)IN * kHid : 0) + (size_t)kDirWarps * IN + 3 * kHid);
+  auto kern = k_direct<DV, FLOW>;
+  if (set_smem(kern, sm) != cudaSuccess) return -1;
+  const int per_sm = std::max(1, blocks_per_sm((const void *)kern, 32 * kDirWarps, sm));
+  const int64_t blocks = (nK + kDirWarps - 1) / kDirWarps;
+  const int grid = (int)std::min<int64_t>(blocks, (int64_t)num_sms() * per_sm);
+  kern<<<grid, 32 * kDirWarps, sm, s>>>(ev, K, nK, g, tb, acc, cnt, mlp, out, err);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -857,6 +1108,21 @@ int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
                   const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
   VECKM_DISPATCH_DV(g.U, (pixsum_impl<DV>(g, tb, nsorted, rec, rpix, n, acc, s)));
+}
+
+int launch_pixsum_owned(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
+                        const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
+  VECKM_DISPATCH_DV(g.U, (pixsum_owned_impl<DV>(tb, nsorted, rec, rpix, n, acc, s)));
+}
+
+int launch_direct(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
+                  const Tables &tb, const float4 *acc, const int *cnt, const MLP *mlp, float *out,
+                  int *err, cudaStream_t s) {
+  if (mlp) {
+    if (g.U > 64) return -2;  // W1 transposed in shared memory: 2D x 128 floats
+    VECKM_DISPATCH_DV(g.U, (direct_impl<DV, true>(ev, K, nK, g, tb, acc, cnt, *mlp, out, err, s)));
+  }
+  VECKM_DISPATCH_DV(g.U, (direct_impl<DV, false>(ev, K, nK, g, tb, acc, cnt, MLP{}, out, err, s)));
 }
 
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,

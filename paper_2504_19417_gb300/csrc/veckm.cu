@@ -104,7 +104,7 @@ void free_all(veckm_ctx *c) {
   void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
                   c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
                   c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->cx, c->cy, c->ct,
-                  c->slice_tab, c->wxy};
+                  c->slice_tab, c->wxy, c->rx, c->ry};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -186,10 +186,21 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   const bool sorted = (what == Out::Flow) && K == nullptr;
   if (veckm_status st = ensure_records(c, n, s)) return st;
   int launches = 0, r;
+  // Dense pooling or the direct window form, by the runtime model of Eq.
+  // runtime (Section 2.2.2): the dense passes cost per pixel, the direct form
+  // per requested flow and window pixel.  The direct perceptron is the FP32
+  // one (D <= 128).
+  const double area = (2.0 * g.dx + 1) * (2.0 * g.dy + 1);
+  const double t_dense = c->k_pixel * (double)P + c->k_flow_dense * (double)nK;
+  const double t_direct = c->k_flow_window * area * (double)nK;
+  const bool direct_ok = what == Out::Emb || g.D <= 128;
+  const bool direct = direct_ok && (c->path == VECKM_PATH_DIRECT ||
+                                    (c->path == VECKM_PATH_AUTO && t_direct < t_dense));
+  c->last_path = direct ? VECKM_PATH_DIRECT : VECKM_PATH_DENSE;
   mark();
   cudaError_t e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "clearing the counts");
-  if ((r = launch_hist(ev, g, c->cnt, c->err, sorted ? out : nullptr, s)) < 0)
+  if ((r = launch_hist(ev, g, c->cnt, c->err, (sorted && !direct) ? out : nullptr, s)) < 0)
     return cuda_fail(cudaGetLastError(), "histogram launch");
   launches += r;
   if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s)) < 0)
@@ -199,6 +210,24 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     return cuda_fail(cudaGetLastError(), "placement launch");
   launches += r;
   mark();
+  if (direct) {
+    if ((r = launch_pixsum_owned(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s)) < 0)
+      return cuda_fail(cudaGetLastError(), "pixel sum launch");
+    launches += r;
+    mark();
+    mark();  // no row pass, window counts or column pass
+    mark();
+    mark();
+    MLP m = c->mlp();
+    if ((r = launch_direct(ev, K, nK, g, tb, c->acc, c->cnt, what == Out::Flow ? &m : nullptr,
+                           out, c->err, s)) < 0)
+      return cuda_fail(cudaGetLastError(), "direct window launch");
+    launches += r;
+    mark();
+    if (c->timing) c->pending.push_back(evs);
+    c->last_launches = launches;
+    return VECKM_OK;
+  }
   if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s)) < 0)
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
@@ -333,6 +362,8 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   std::vector<float> hty = phase_rows(c->Y, wy, 0, g.H, 1);
   std::vector<float> hsx = phase_rows(c->X, wx, 1, 1, 1);
   std::vector<float> hsy = phase_rows(c->Y, wy, 1, 1, 1);
+  std::vector<float> hrx = phase_rows(c->X, wx, -cfg->dx, 2 * (int64_t)cfg->dx + 1, 1);
+  std::vector<float> hry = phase_rows(c->Y, wy, -cfg->dy, 2 * (int64_t)cfg->dy + 1, 1);
   // frequencies in turns per unit (microsecond, pixel), reduced to
   // [-1/2, 1/2], as 64-bit fixed point (the device reduces q * w mod 1
   // exactly for an integer q)
@@ -367,6 +398,8 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(dalloc(&c->sx, (size_t)g.U));
   VK_TRY(dalloc(&c->sy, (size_t)g.U));
   VK_TRY(dalloc(&c->ty, (size_t)g.H * g.U));
+  VK_TRY(dalloc(&c->rx, (2 * (size_t)cfg->dx + 1) * g.U));
+  VK_TRY(dalloc(&c->ry, (2 * (size_t)cfg->dy + 1) * g.U));
   VK_TRY(dalloc(&c->wt, (size_t)D));
   VK_TRY(dalloc(&c->wxy, 2 * (size_t)D));
   VK_TRY(dalloc(&c->W1, (size_t)c->hidden * IN));
@@ -390,6 +423,8 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(cudaMemcpy(c->ty, hty.data(), hty.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->sx, hsx.data(), hsx.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->sy, hsy.data(), hsy.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->rx, hrx.data(), hrx.size() * 4, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->ry, hry.data(), hry.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->wt, hwt.data(), hwt.size() * sizeof(uint2), cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->wxy, hwxy.data(), hwxy.size() * sizeof(uint2), cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1, c->hW1.data(), c->hW1.size() * 4, cudaMemcpyHostToDevice));
@@ -544,6 +579,27 @@ veckm_status veckm_stage_times(veckm_ctx *c, double *ms, int64_t *launches, int 
 }
 
 int veckm_last_launch_count(const veckm_ctx *c) { return c ? c->last_launches : 0; }
+
+veckm_status veckm_set_path(veckm_ctx *c, int32_t path) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  if (path != VECKM_PATH_AUTO && path != VECKM_PATH_DENSE && path != VECKM_PATH_DIRECT)
+    return fail(VECKM_EINVAL, "unknown path %d", path);
+  c->path = path;
+  return VECKM_OK;
+}
+
+int veckm_last_path(const veckm_ctx *c) { return c ? c->last_path : 0; }
+
+veckm_status veckm_set_path_model(veckm_ctx *c, double pixel_ns, double flow_dense_ns,
+                                  double flow_window_ns) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  if (!(pixel_ns > 0) || !(flow_dense_ns >= 0) || !(flow_window_ns > 0))
+    return fail(VECKM_EINVAL, "model coefficients must be positive");
+  c->k_pixel = pixel_ns * 1e-9;
+  c->k_flow_dense = flow_dense_ns * 1e-9;
+  c->k_flow_window = flow_window_ns * 1e-9;
+  return VECKM_OK;
+}
 
 }  // extern "C"
 

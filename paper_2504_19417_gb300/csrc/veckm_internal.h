@@ -33,6 +33,8 @@ struct Tables {
   const float4 *sy;     // [U]         exp(i Y/dy), one step along y
   const uint2 *wt;      // [D]         T_d/(2 pi dt) in turns per microsecond, reduced to
                         //             [-1/2, 1/2], as 64-bit fixed point (lo, hi words)
+  const float4 *rx;     // [2dx + 1][U] exp(i o X/dx), offset o in [-dx, dx], row o + dx
+  const float4 *ry;     // [2dy + 1][U] exp(i o Y/dy), offset o in [-dy, dy], row o + dy
 };
 
 struct MLP {
@@ -95,6 +97,15 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
                       int *err, cudaStream_t s, const Tune &tn = Tune{});
+
+// Direct window form: per-pixel sums written once per occupied pixel (no
+// clear), then one warp per requested event summing its window (mlp == NULL:
+// the encoding to out [nK][2D]; else the flows to out [nK][2], D <= 128).
+int launch_pixsum_owned(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
+                        const int *rpix, int64_t n, float4 *acc, cudaStream_t s);
+int launch_direct(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
+                  const Tables &tb, const float4 *acc, const int *cnt, const MLP *mlp, float *out,
+                  int *err, cudaStream_t s);
 
 int num_sms();
 

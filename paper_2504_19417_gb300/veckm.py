@@ -20,6 +20,7 @@ from . import build as _build
 VECKM_OK, VECKM_EINVAL, VECKM_ENOMEM, VECKM_ECUDA = 0, -1, -2, -3
 VECKM_ERANGE, VECKM_ETIMEOUT, VECKM_EBUSY, VECKM_EUNSUPPORTED = -4, -5, -6, -7
 MLP_FP32, MLP_BF16, MLP_FP16 = 0, 1, 2
+PATH_AUTO, PATH_DENSE, PATH_DIRECT = 0, 1, 2
 ACC_FP16 = 4  # or-ed with MLP_BF16 / MLP_FP16: FP16 storage of the normalised pooled grid
 STAGES = ("sort", "pixsum", "pool_rows", "counts", "pool_cols", "gather")
 
@@ -76,7 +77,8 @@ EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noallo
            "veckm_encode_batch", "veckm_plan_create", "veckm_plan_launch",
            "veckm_plan_kernel_count", "veckm_plan_destroy", "veckm_autotune",
            "veckm_server_create", "veckm_server_submit", "veckm_server_poll", "veckm_server_drain",
-           "veckm_server_get_stats", "veckm_server_destroy", "veckm_kde_query", "veckm_normals")
+           "veckm_server_get_stats", "veckm_server_destroy", "veckm_kde_query", "veckm_set_path",
+           "veckm_last_path", "veckm_set_path_model", "veckm_normals")
 
 
 def library_path() -> str:
@@ -124,6 +126,9 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_server_destroy.argtypes = [P]
     lib.veckm_server_destroy.restype = None
     lib.veckm_kde_query.argtypes = [P, P, i64, P, P, P, P, i64, P, P]
+    lib.veckm_set_path.argtypes = [P, i32]
+    lib.veckm_last_path.argtypes = [P]
+    lib.veckm_set_path_model.argtypes = [P, C.c_double, C.c_double, C.c_double]
     for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
                  "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
                  "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count",
@@ -131,7 +136,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
                  "veckm_plan_create", "veckm_plan_launch", "veckm_plan_kernel_count",
                  "veckm_autotune", "veckm_server_create", "veckm_server_submit",
                  "veckm_server_poll", "veckm_server_drain", "veckm_server_get_stats",
-                 "veckm_kde_query"):
+                 "veckm_kde_query", "veckm_set_path", "veckm_last_path",
+                 "veckm_set_path_model"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -484,6 +490,15 @@ class Encoder:
             out = torch.empty((N, 2 if predict else 2 * self.p.D), dtype=torch.float32,
                               device="cuda")
         return Plan(self, slices, out, predict)
+
+    def set_path(self, path: int):
+        _check(lib().veckm_set_path(self._h, path))
+
+    def last_path(self) -> int:
+        return int(lib().veckm_last_path(self._h))
+
+    def set_path_model(self, pixel_ns: float, flow_dense_ns: float, flow_window_ns: float):
+        _check(lib().veckm_set_path_model(self._h, pixel_ns, flow_dense_ns, flow_window_ns))
 
     def kde_query(self, emb, rows, qt, qx, qy, out=None, stream=None):
         """Lemma 1 read-back at integer offsets (qt us, qx, qy px) from the events of emb rows."""
