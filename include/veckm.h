@@ -287,6 +287,46 @@ void veckm_plan_destroy(veckm_plan *plan);
 veckm_status veckm_autotune(veckm_ctx *ctx, int32_t width, int32_t height, void *stream,
                             int32_t *tuned);
 
+/* ------------------------------------------------------------------ streams
+ * Sliding-window encoding of one sensor's event stream (not in the paper's
+ * implementation; it follows from the linearity of the accumulation of
+ * Algorithm 1).  A stream keeps its window's per-pixel phase sums and counts
+ * resident on the device and updates them per pushed packet: the packet's
+ * events are added and the events that left the window subtracted.  The sums
+ * are held in 64-bit fixed point, into which every FP32 phase converts
+ * exactly, so the resident sums stay bit-identical to sums built from the
+ * window's events alone, however many packets pass (no drift, no rebuild).
+ * The context supplies the sensor, D, the window radii, dt, the weights and
+ * its scratch buffers; calls on a stream and on its context are ordered on
+ * one CUDA stream. */
+typedef struct veckm_stream veckm_stream;
+
+/* window_us: the window length (events with t >= t_hi - window_us stay);
+ * capacity: the most events the window may hold (the device ring).  Allocates
+ * 32 D bytes per pixel plus 16 bytes per ring slot. */
+veckm_status veckm_stream_create(veckm_ctx *ctx, int64_t window_us, int64_t capacity,
+                                 veckm_stream **out);
+/* Push a packet of n events (device x, y int16; t uint32 microseconds, the
+ * stream's absolute times, sorted, all >= the previous packet's) that ends
+ * at t_hi_us.  The window becomes [t_hi_us - window_us, t_hi_us]; the
+ * packet's events are encoded against it (predict == 0: d_out float
+ * [n][2D] encodings; else d_out float [n][2] flows).  An event outside the
+ * sensor or the window, or out of time order, is not added and its output
+ * row is zeroed (VECKM_ERANGE at the next status check); events beyond the
+ * ring's capacity likewise (VECKM_EBUSY).  Never synchronises.  n may be 0
+ * (the window still slides to t_hi_us). */
+veckm_status veckm_stream_push(veckm_stream *st, const int16_t *d_x, const int16_t *d_y,
+                               const uint32_t *d_t, int64_t n, uint32_t t_hi_us, float *d_out,
+                               int32_t predict, void *stream);
+/* Events currently in the window (synchronises the stream). */
+veckm_status veckm_stream_window(veckm_stream *st, int64_t *h_events, void *stream);
+/* Copy the resident sums (int64 [H][W][D/2][4]: re(2u), im(2u), re(2u+1),
+ * im(2u+1) in units of 2^-32) and counts (int32 [H][W]) to host memory
+ * (synchronises the stream). */
+veckm_status veckm_stream_accumulator(veckm_stream *st, int64_t *h_acc, int32_t *h_cnt,
+                                      void *stream);
+void veckm_stream_destroy(veckm_stream *st);
+
 /* ------------------------------------------------------------------ serving
  * A request loop for event packets from many sensors.  Each packet is one
  * slice (its events, its sensor size and its start).  veckm_server_submit

@@ -1,0 +1,346 @@
+// Sliding-window streams: a per-stream resident accumulator over the last
+// `window` microseconds of a sensor's events.
+//
+// The accumulation of Algorithm 1 (PixelEmbed, PixelCount) is linear in the
+// events, so a window that slides is kept up to date by adding the events of
+// each new packet and subtracting the events that leave the window.  To keep
+// that exact over any number of packets the per-pixel sums are held in 64-bit
+// fixed point: every component of an event's FP32 phase exp(i t T_d/dt) is an
+// integer multiple of 2^-32 (at most 24 significant bits, magnitude at most
+// one), so v * 2^32 converts to int64 without rounding, and integer addition
+// is exact and independent of order.  After any sequence of packets the
+// accumulator equals, bit for bit, the one built from the window's events
+// alone.  Counts are exact int32.
+//
+// The stream's valid events live in a device ring (x, y, t; t in absolute
+// microseconds), in time order as long as packets arrive in time order and
+// are each sorted by time (event cameras emit them so; an event earlier than
+// its predecessor in the packet is rejected).  A packet is pushed with its
+// end time t_hi (every event has t <= t_hi); the window is then
+// [t_hi - window, t_hi].  A push, in stream order:
+//   1. flag the packet's valid events (inside the sensor and the window, in
+//      order) and scan the flags: the valid events' places in the ring;
+//   2. find the first ring event still in the window (binary search) and how
+//      many valid events fit the ring after the expiry;
+//   3. subtract the events that left;
+//   4. append the valid events that fit (K[i] = an event's ring slot, or -1:
+//      its output row is zeroed and the error word set);
+//   5. add them;
+//   6. convert the accumulator to the FP32 grid and run the pooling and the
+//      gather (and perceptron) for the packet's events.
+// Nothing is copied to the host: a push never synchronises.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ctx.h"
+#include "phase.cuh"
+
+namespace veckm {
+namespace {
+
+struct RingState {
+  long long head;      // events appended so far (ring position = index mod capacity)
+  long long tail;      // first event still in the window
+  long long tail_old;  // the tail before the current push
+  long long head_old;  // the head before the current push
+  long long app;       // events of the current packet that fit the ring
+};
+
+__device__ __forceinline__ void red_add_s64(long long *p, long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)v) : "memory");
+}
+
+// 1. valid events of the packet (inside the sensor and [t_lo, t_hi], not
+// earlier than the event before them)
+__global__ void k_ring_flags(const int16_t *__restrict__ x, const int16_t *__restrict__ y,
+                             const uint32_t *__restrict__ t, long long n, int W, int H,
+                             uint32_t t_lo, uint32_t t_hi, int *__restrict__ flag, int *err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int xi = x[i], yi = y[i];
+  const uint32_t ti = t[i];
+  const bool ok = xi >= 0 && xi < W && yi >= 0 && yi < H && ti >= t_lo && ti <= t_hi &&
+                  (i == 0 || t[i - 1] <= ti);
+  if (!ok) atomicOr(err, ERR_EVENT_RANGE);
+  flag[i] = ok ? 1 : 0;
+}
+
+// 2. new tail: the first ring event with t >= t_lo (ring events ascend in
+// t); then how many of the `*nvalid` valid packet events fit the ring
+__global__ void k_ring_tail(RingState *st, const uint32_t *__restrict__ rt, long long cap,
+                            uint32_t t_lo, const int *__restrict__ nvalid) {
+  const long long n = nvalid ? *nvalid : 0;
+  if (threadIdx.x != 0) return;
+  long long lo = st->tail, hi = st->head;
+  st->tail_old = lo;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (rt[mid % cap] < t_lo) lo = mid + 1;
+    else hi = mid;
+  }
+  st->tail = lo;
+  st->head_old = st->head;
+  const long long room = cap - (st->head - lo);
+  st->app = n < room ? n : room;
+}
+
+// 3./5. subtract (sign -1: ring events [tail_old, tail)) or add (+1: the
+// appended events [head_old, head_old + app)) their fixed-point phases and
+// counts.  One warp per event, lanes over units (channels 2u, 2u+1).
+template <int DV>
+__global__ void __launch_bounds__(256)
+    k_ring_apply(const RingState *st, int sign,
+                 const int16_t *__restrict__ rx, const int16_t *__restrict__ ry,
+                 const uint32_t *__restrict__ rt, long long cap, int W, int U,
+                 const uint2 *__restrict__ wt, long long *__restrict__ acc64,
+                 int *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const long long first = sign < 0 ? st->tail_old : st->head_old;
+  const long long count = sign < 0 ? st->tail - st->tail_old : st->app;
+  uint2 w[DV][2];
+#pragma unroll
+  for (int v = 0; v < DV; ++v) {
+    const int u = lane + 32 * v;
+    w[v][0] = __ldg(wt + 2 * u);
+    w[v][1] = __ldg(wt + 2 * u + 1);
+  }
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < count;
+       j += nw) {
+    const long long pos = (first + j) % cap;
+    const int p = ry[pos] * W + rx[pos];
+    const uint32_t t = rt[pos];
+    long long *dst = acc64 + (size_t)p * 4 * U;
+#pragma unroll
+    for (int v = 0; v < DV; ++v) {
+      const int u = lane + 32 * v;
+      const float4 ph = time_phase2(t, w[v][0], w[v][1]);  // (re, im) of channels 2u, 2u+1
+      const float sc = 4294967296.0f * (float)sign;         // exact: a power of two
+      red_add_s64(dst + 4 * u + 0, (long long)(ph.x * sc));
+      red_add_s64(dst + 4 * u + 1, (long long)(ph.y * sc));
+      red_add_s64(dst + 4 * u + 2, (long long)(ph.z * sc));
+      red_add_s64(dst + 4 * u + 3, (long long)(ph.w * sc));
+    }
+    if (lane == 0) atomicAdd(cnt + p, sign);
+  }
+}
+
+// 4. append valid event i (place off[i] among the valid ones) at ring
+// position head + off[i] if it fits; K[i] = its ring slot, else -1 (an
+// index outside the ring: the gather writes zeros for it)
+__global__ void k_ring_append(const RingState *st, const int16_t *__restrict__ x,
+                              const int16_t *__restrict__ y, const uint32_t *__restrict__ t,
+                              long long n, const int *__restrict__ flag,
+                              const int *__restrict__ off, int16_t *__restrict__ rx,
+                              int16_t *__restrict__ ry, uint32_t *__restrict__ rt, long long cap,
+                              int64_t *__restrict__ K, int *err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!flag[i]) {
+    K[i] = -1;
+    return;
+  }
+  if (off[i] >= st->app) {  // the window would hold more events than the ring
+    atomicOr(err, ERR_CAPACITY);
+    K[i] = -1;
+    return;
+  }
+  const long long r = (st->head_old + off[i]) % cap;
+  rx[r] = x[i];
+  ry[r] = y[i];
+  rt[r] = t[i];
+  K[i] = r;
+}
+
+__global__ void k_ring_advance(RingState *st) {
+  if (threadIdx.x == 0) st->head = st->head_old + st->app;
+}
+
+// 6. the window's accumulator as the FP32 grid of the pooling passes
+__global__ void k_fixed_to_float(const long long *__restrict__ acc64, float4 *__restrict__ acc,
+                                 long long units) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= units) return;
+  const longlong2 a = reinterpret_cast<const longlong2 *>(acc64)[2 * i];
+  const longlong2 b = reinterpret_cast<const longlong2 *>(acc64)[2 * i + 1];
+  const float s = 2.3283064365386963e-10f;  // 2^-32
+  acc[i] = make_float4(__ll2float_rn(a.x) * s, __ll2float_rn(a.y) * s, __ll2float_rn(b.x) * s,
+                       __ll2float_rn(b.y) * s);
+}
+
+}  // namespace
+}  // namespace veckm
+
+using namespace veckm;
+
+struct veckm_stream {
+  veckm_ctx *c = nullptr;
+  int64_t window = 0, cap = 0;
+  long long *acc64 = nullptr;
+  int *cnt = nullptr;
+  int16_t *rx = nullptr, *ry = nullptr;
+  uint32_t *rt = nullptr;
+  int64_t *K = nullptr;
+  RingState *st = nullptr;
+  int *flag = nullptr, *off = nullptr, *cur = nullptr, *bsum = nullptr, *nvalid = nullptr;
+};
+
+extern "C" {
+
+veckm_status veckm_stream_create(veckm_ctx *c, int64_t window_us, int64_t capacity,
+                                 veckm_stream **out) {
+  if (!out) return fail_msg(VECKM_EINVAL, "null output");
+  *out = nullptr;
+  if (!c) return fail_msg(VECKM_EINVAL, "null context");
+  if (window_us < 0 || window_us > 0xffffffffLL) return fail_msg(VECKM_EINVAL, "window outside 0..2^32-1 us");
+  if (capacity < 1 || capacity > VECKM_MAX_EVENTS) return fail_msg(VECKM_EINVAL, "capacity outside 1..2^30");
+  veckm_stream *s = new (std::nothrow) veckm_stream();
+  if (!s) return fail_msg(VECKM_ENOMEM, "host allocation");
+  s->c = c;
+  s->window = window_us;
+  s->cap = capacity;
+  const size_t P = (size_t)c->g.W * c->g.H;
+  cudaError_t e = cudaMalloc(&s->acc64, P * (size_t)c->g.U * 4 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&s->cnt, P * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&s->rx, (size_t)capacity * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&s->ry, (size_t)capacity * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&s->rt, (size_t)capacity * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->K, (size_t)capacity * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(RingState));
+  if (e == cudaSuccess) e = cudaMalloc(&s->flag, (size_t)capacity * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->off, ((size_t)capacity + 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->cur, (size_t)capacity * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->bsum, (size_t)scan_blocks(capacity) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->nvalid, 4);
+  if (e == cudaSuccess) e = cudaMemset(s->acc64, 0, P * (size_t)c->g.U * 4 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(s->cnt, 0, P * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(s->st, 0, sizeof(RingState));
+  if (e != cudaSuccess) {
+    veckm_stream_destroy(s);
+    return fail_cuda(e, "stream buffers");
+  }
+  *out = s;
+  return VECKM_OK;
+}
+
+veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_t *d_y,
+                               const uint32_t *d_t, int64_t n, uint32_t t_hi_us, float *d_out,
+                               int32_t predict, void *stream) {
+  if (!s) return fail_msg(VECKM_EINVAL, "null stream");
+  if (n < 0 || n > s->cap) return fail_msg(VECKM_EINVAL, "packet of %lld events for a ring of %lld", (long long)n, (long long)s->cap);
+  if (n > 0 && (!d_x || !d_y || !d_t || !d_out)) return fail_msg(VECKM_EINVAL, "null buffer");
+  veckm_ctx *c = s->c;
+  const Geometry &g = c->g;
+  if (predict && g.D > 128 && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)))
+    return fail_msg(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
+  cudaStream_t cs = (cudaStream_t)stream;
+  const uint32_t t_lo = t_hi_us >= (uint64_t)s->window ? t_hi_us - (uint32_t)s->window : 0u;
+  const int DV = g.U / 32;
+  auto apply = [&](int sign) {
+    const int blocks = num_sms() * 8;
+    switch (DV) {
+      case 1: k_ring_apply<1><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
+      case 2: k_ring_apply<2><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
+      case 3: k_ring_apply<3><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
+      default: k_ring_apply<4><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
+    }
+  };
+  int launches = 0;
+  // 1. valid events and their places
+  if (n > 0) {
+    k_ring_flags<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(d_x, d_y, d_t, n, g.W, g.H, t_lo, t_hi_us, s->flag, c->err);
+    Geometry line{};
+    line.W = (int)n;
+    line.H = 1;
+    const int r = launch_scan(line, s->flag, s->bsum, s->off, s->cur, s->nvalid, cs);
+    if (r < 0) return fail_cuda(cudaGetLastError(), "stream scan launch");
+    launches += 1 + r;
+  }
+  // 2-3. expire
+  k_ring_tail<<<1, 32, 0, cs>>>(s->st, s->rt, s->cap, t_lo, n > 0 ? s->nvalid : nullptr);
+  apply(-1);
+  launches += 2;
+  // 4-5. append and add
+  if (n > 0) {
+    k_ring_append<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(s->st, d_x, d_y, d_t, n, s->flag, s->off, s->rx, s->ry, s->rt, s->cap, s->K, c->err);
+    apply(+1);
+    launches += 2;
+  }
+  k_ring_advance<<<1, 32, 0, cs>>>(s->st);
+  launches += 1;
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail_cuda(e, "stream update launch");
+  }
+  if (n == 0) {
+    c->last_launches = launches;
+    return VECKM_OK;
+  }
+  // 6. the window's grid, pooling, then the packet's outputs
+  const long long units = (long long)g.W * g.H * g.U;
+  k_fixed_to_float<<<(unsigned)((units + 255) / 256), 256, 0, cs>>>(s->acc64, c->acc, units);
+  launches += 1;
+  const Tables tb = c->tables();
+  const Tune tn = c->tune_for(g);
+  int r;
+  if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, cs, tn)) < 0) return fail_cuda(cudaGetLastError(), "pooling (rows) launch");
+  launches += r;
+  if ((r = launch_counts(g, s->cnt, c->cnt_tmp, c->ncnt, cs)) < 0) return fail_cuda(cudaGetLastError(), "window count launch");
+  launches += r;
+  const Events ev{s->rx, s->ry, s->rt, s->cap, 0u, 0xffffffffu};
+  const bool half_grid = predict && (c->flags & VECKM_ACC_FP16);
+  r = half_grid ? launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, cs, tn)
+                : launch_pool_cols(g, tb, c->hbuf, c->acc, cs, tn);
+  if (r < 0) return fail_cuda(cudaGetLastError(), "pooling (columns) launch");
+  launches += r;
+  if (!predict) {
+    r = launch_gather_emb(ev, s->K, n, g, tb, c->acc, c->ncnt, d_out, c->err, cs);
+  } else if (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)) {
+    MLP m = c->mlp();
+    m.pooled_half = half_grid ? 1 : 0;
+    r = launch_predict_tc(ev, s->K, n, nullptr, nullptr, nullptr, g, tb, c->acc, c->ncnt, m,
+                          d_out, c->err, cs, tn);
+  } else {
+    r = launch_predict_fp32(ev, s->K, n, nullptr, nullptr, nullptr, g, tb, c->acc, c->ncnt,
+                            c->mlp(), d_out, c->err, cs);
+    if (r == -2) return fail_msg(VECKM_EUNSUPPORTED, "FP32 perceptron supports D <= 128");
+  }
+  if (r < 0) return fail_cuda(cudaGetLastError(), "gather launch");
+  c->last_launches = launches + r;
+  return VECKM_OK;
+}
+
+veckm_status veckm_stream_window(veckm_stream *s, int64_t *h_events, void *stream) {
+  if (!s || !h_events) return fail_msg(VECKM_EINVAL, "null argument");
+  RingState h{};
+  cudaError_t e = cudaMemcpyAsync(&h, s->st, sizeof h, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail_cuda(e, "stream state");
+  *h_events = h.head - h.tail;
+  return VECKM_OK;
+}
+
+veckm_status veckm_stream_accumulator(veckm_stream *s, int64_t *h_acc, int32_t *h_cnt, void *stream) {
+  if (!s || !h_acc || !h_cnt) return fail_msg(VECKM_EINVAL, "null argument");
+  const size_t P = (size_t)s->c->g.W * s->c->g.H;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h_acc, s->acc64, P * (size_t)s->c->g.U * 4 * 8, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, s->cnt, P * 4, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  return e == cudaSuccess ? VECKM_OK : fail_cuda(e, "stream accumulator copy");
+}
+
+void veckm_stream_destroy(veckm_stream *s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  void *ptrs[] = {s->acc64, s->cnt, s->rx, s->ry, s->rt, s->K, s->st,
+                  s->flag, s->off, s->cur, s->bsum, s->nvalid};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+}  // extern "C"

@@ -491,6 +491,7 @@ veckm_status veckm_sync_status(veckm_ctx *c, void *stream) {
   if (e != cudaSuccess) return cuda_fail(e, "veckm_sync_status");
   const int w = *c->h_err;
   if (w & ERR_TIMEOUT) return fail(VECKM_ETIMEOUT, "a bounded device wait ran out");
+  if (w & ERR_CAPACITY) return fail(VECKM_EBUSY, "a stream's window held more events than its ring");
   if (w & (ERR_EVENT_RANGE | ERR_INDEX_RANGE))
     return fail(VECKM_ERANGE, "%s%s", (w & ERR_EVENT_RANGE) ? "event outside the sensor or time span; " : "",
                 (w & ERR_INDEX_RANGE) ? "index in K outside [0, n)" : "");

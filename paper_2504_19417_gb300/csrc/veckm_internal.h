@@ -8,7 +8,7 @@
 namespace veckm {
 
 // Bits of the device error word.
-enum : int { ERR_EVENT_RANGE = 1, ERR_INDEX_RANGE = 2, ERR_TIMEOUT = 4 };
+enum : int { ERR_EVENT_RANGE = 1, ERR_INDEX_RANGE = 2, ERR_TIMEOUT = 4, ERR_CAPACITY = 8 };
 
 // Device view of one slice's events.
 struct Events {

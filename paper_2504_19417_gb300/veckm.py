@@ -78,7 +78,9 @@ EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noallo
            "veckm_plan_kernel_count", "veckm_plan_destroy", "veckm_autotune",
            "veckm_server_create", "veckm_server_submit", "veckm_server_poll", "veckm_server_drain",
            "veckm_server_get_stats", "veckm_server_destroy", "veckm_kde_query", "veckm_set_path",
-           "veckm_last_path", "veckm_set_path_model", "veckm_normals")
+           "veckm_last_path", "veckm_set_path_model", "veckm_stream_create", "veckm_stream_push",
+           "veckm_stream_window", "veckm_stream_accumulator", "veckm_stream_destroy",
+           "veckm_normals")
 
 
 def library_path() -> str:
@@ -129,6 +131,12 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_set_path.argtypes = [P, i32]
     lib.veckm_last_path.argtypes = [P]
     lib.veckm_set_path_model.argtypes = [P, C.c_double, C.c_double, C.c_double]
+    lib.veckm_stream_create.argtypes = [P, i64, i64, C.POINTER(C.c_void_p)]
+    lib.veckm_stream_push.argtypes = [P, P, P, P, i64, C.c_uint32, P, i32, P]
+    lib.veckm_stream_window.argtypes = [P, P, P]
+    lib.veckm_stream_accumulator.argtypes = [P, P, P, P]
+    lib.veckm_stream_destroy.argtypes = [P]
+    lib.veckm_stream_destroy.restype = None
     for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
                  "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
                  "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count",
@@ -137,7 +145,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
                  "veckm_autotune", "veckm_server_create", "veckm_server_submit",
                  "veckm_server_poll", "veckm_server_drain", "veckm_server_get_stats",
                  "veckm_kde_query", "veckm_set_path", "veckm_last_path",
-                 "veckm_set_path_model"):
+                 "veckm_set_path_model", "veckm_stream_create", "veckm_stream_push",
+                 "veckm_stream_window", "veckm_stream_accumulator"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -340,6 +349,53 @@ class Server:
             lib().veckm_server_destroy(self._h)
             self._h = None
             self._bufs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """A sliding window over one sensor's events (veckm_stream_*), on an Encoder's context."""
+
+    def __init__(self, enc, window_us: int, capacity: int):
+        h = C.c_void_p()
+        _check(lib().veckm_stream_create(enc.handle, window_us, capacity, C.byref(h)))
+        self._h = h
+        self.enc = enc
+
+    def push(self, x, y, t, t_hi: int, out=None, predict: bool = True, stream=None):
+        import torch
+        n = x.numel()
+        if out is None:
+            out = torch.empty((n, 2 if predict else 2 * self.enc.p.D), dtype=torch.float32,
+                              device="cuda")
+        d = Encoder._dev
+        _check(lib().veckm_stream_push(self._h, d(x, torch.int16), d(y, torch.int16),
+                                       d(t, torch.int32), n, C.c_uint32(t_hi),
+                                       d(out, torch.float32), 1 if predict else 0,
+                                       Encoder._stream(stream)))
+        return out
+
+    def window_events(self, stream=None) -> int:
+        v = C.c_int64()
+        _check(lib().veckm_stream_window(self._h, C.byref(v), Encoder._stream(stream)))
+        return v.value
+
+    def accumulator(self, stream=None):
+        p = self.enc.p
+        acc = np.zeros((p.height, p.width, p.D // 2, 4), np.int64)
+        cnt = np.zeros((p.height, p.width), np.int32)
+        _check(lib().veckm_stream_accumulator(self._h, _np_ptr(acc), _np_ptr(cnt),
+                                              Encoder._stream(stream)))
+        return acc, cnt
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().veckm_stream_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:
