@@ -178,7 +178,7 @@ veckm_status veckm_stage_times(veckm_ctx *ctx, double *ms, int64_t *calls, int n
 int veckm_last_launch_count(const veckm_ctx *ctx);
 
 /* Dense pooling or the direct window form.  Algorithm 1 computes each
- * requested flow by looping over its window (the paper's Lines 11-21, cost C
+ * requested flow by looping over its window (its second loop, cost C
  * per flow in Eq. runtime of Section 2.2.2).  The dense form pools every
  * pixel once with separable box sums (cost per pixel, then little per flow);
  * the direct form keeps the window loop, visiting only occupied window pixels
