@@ -301,10 +301,15 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       }
     };
     auto compute = [&](int par, int j0, const Q(&q)[kB][DV], uint32_t Abuf) {
+      // every t of the batch first; plain stores let the rows interleave
+      uint32_t tjs[kB];
+#pragma unroll
+      for (int r = 0; r < kB; ++r) tjs[r] = (uint32_t)ms[par * kRowsPerWarp + j0 + r].y;
+      uint8_t *Ag = sA + (Abuf - sA_a);
 #pragma unroll
       for (int r = 0; r < kB; ++r) {
         const int j = j0 + r;
-        const uint32_t tj = (uint32_t)ms[par * kRowsPerWarp + j].y;
+        const uint32_t tj = tjs[r];
 #pragma unroll
         for (int v = 0; v < DV; ++v) {
           const float4 ph = time_phase2(tj, wf[v][0], wf[v][1]);  // (c0, s0, c1, s1)
@@ -330,8 +335,8 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
             wre = pack2(e.x, e.z, fp16);
             wim = pack2(e.y, e.w, fp16);
           }
-          const uint32_t addr = ((Abuf + lo[v]) ^ (uint32_t)((j & 7) * 0x90)) + (j >> 3) * 1024;
-          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(wre), "r"(wim) : "memory");
+          *reinterpret_cast<uint2 *>(Ag + ((lo[v] ^ (uint32_t)((j & 7) * 0x90)) + (j >> 3) * 1024)) =
+              make_uint2(wre, wim);
         }
       }
     };
