@@ -759,7 +759,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--mode", default="fp16-acc16",
+    ap.add_argument("--mode", default="fp16",
                     choices=["bf16", "fp16", "fp32", "fp16-acc16", "bf16-acc16"])
     ap.add_argument("--lean", action="store_true", help="timed device loop only (for profilers)")
     ap.add_argument("--scale", type=float, default=1.0, help="events x scale (profiling cases)")
