@@ -148,6 +148,31 @@ veckm_status veckm_predict_host(veckm_ctx *ctx, const int16_t *h_x, const int16_
                                 const uint32_t *h_t, int64_t n, uint32_t t_ref_us,
                                 const int64_t *h_K, int64_t nK, float *h_flow, void *stream);
 
+/* Pipelined form of veckm_predict_host (Eq. 6 on host buffers).  Enqueues
+ * the call and returns at once with *ticket set; the call's result is ready
+ * after veckm_host_wait(ctx, *ticket).  Each context keeps two staging slots
+ * and internal upload, compute and download streams: the uploads of one call
+ * run while the previous call computes, and its flows come back while the
+ * next call computes, so at most two calls are in flight (a third call first
+ * waits for the call two back).  Calls run on the device in the order they were made.  h_x, h_y,
+ * h_t, h_K must stay unchanged and h_flow untouched until the wait; they
+ * should be pinned (cudaHostAlloc), since pageable buffers make the copies
+ * block the host.  Until the last ticket is waited for, the context must not
+ * be used on another stream.  The device error word is read and cleared
+ * after each call, so a ticket's status covers exactly its own call.
+ * Argument errors are returned at once (no ticket is issued). */
+veckm_status veckm_predict_host_async(veckm_ctx *ctx, const int16_t *h_x, const int16_t *h_y,
+                                      const uint32_t *h_t, int64_t n, uint32_t t_ref_us,
+                                      const int64_t *h_K, int64_t nK, float *h_flow,
+                                      int64_t *ticket);
+
+/* Block until the call with this ticket has finished and its flows are in
+ * h_flow; returns its status (VECKM_ERANGE for an out-of-range event or
+ * index, VECKM_ETIMEOUT, a CUDA failure).  A ticket may be waited for more
+ * than once; the statuses of the last 64 tickets are kept (older ones:
+ * VECKM_EINVAL). */
+veckm_status veckm_host_wait(veckm_ctx *ctx, int64_t ticket);
+
 /* Switch the perceptron precision and pooled-grid storage of an existing
  * context (VECKM_MLP_* | VECKM_ACC_FP16); tables and accumulators are kept.
  * Synchronous. */

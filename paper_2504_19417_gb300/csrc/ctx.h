@@ -8,6 +8,7 @@
 #include "veckm_internal.h"
 
 namespace veckm {
+struct HostPipe;  // pipelined host-buffer calls (host_async.cu)
 constexpr int kStages = 6;  // sort, pixel sums, pool rows, counts, pool cols, gather
 }  // namespace veckm
 
@@ -37,6 +38,7 @@ struct veckm_ctx {
   void *st_buf = nullptr;
   size_t st_cap = 0;
   int *h_err = nullptr;  // pinned
+  veckm::HostPipe *pipe = nullptr;  // created by the first asynchronous host call
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
@@ -87,6 +89,11 @@ veckm_status ensure_records(veckm_ctx *c, int64_t n, cudaStream_t s);
 // sensor, or a canvas of packed sensors no larger than the context's.
 veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, const int64_t *K,
                           int64_t nK, float *out, bool flow, cudaStream_t s, const Tune &tn);
+// Argument checks shared by the entry points that take events.
+veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const void *t,
+                               int64_t n, const void *K, int64_t nK, const void *out);
+// Waits for and frees the asynchronous host pipeline (host_async.cu).
+void destroy_pipe(HostPipe *p);
 // Error helpers shared by the entry points (veckm.cu).
 veckm_status fail_msg(veckm_status st, const char *fmt, ...);
 veckm_status fail_cuda(cudaError_t e, const char *what);

@@ -101,6 +101,8 @@ std::vector<uint16_t> w1_core_matrix(const std::vector<float> &W1, int hidden, i
 }
 
 void free_all(veckm_ctx *c) {
+  veckm::destroy_pipe(c->pipe);
+  c->pipe = nullptr;
   void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
                   c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
                   c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->cx, c->cy, c->ct,
@@ -126,6 +128,9 @@ cudaEvent_t take_event(veckm_ctx *c) {
   return e;
 }
 
+}  // namespace
+
+namespace veckm {
 veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const void *t,
                                int64_t n, const void *K, int64_t nK, const void *out) {
   if (!c) return fail(VECKM_EINVAL, "null context");
@@ -140,6 +145,9 @@ veckm_status check_events_args(veckm_ctx *c, const void *x, const void *y, const
   if (nK > 0 && n == 0) return fail(VECKM_EINVAL, "nK > 0 with an empty slice");
   return VECKM_OK;
 }
+}  // namespace veckm
+
+namespace {
 
 }  // namespace
 

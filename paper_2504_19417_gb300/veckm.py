@@ -11,7 +11,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 from dataclasses import dataclass
-from typing import Optional
+from typing import Optional, Tuple
 
 import numpy as np
 
@@ -71,7 +71,8 @@ class _Slice(C.Structure):
 
 
 EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noalloc", "veckm_predict",
-           "veckm_predict_host", "veckm_set_mlp_mode", "veckm_sync_status", "veckm_last_error",
+           "veckm_predict_host", "veckm_predict_host_async", "veckm_host_wait",
+           "veckm_set_mlp_mode", "veckm_sync_status", "veckm_last_error",
            "veckm_get_frequencies", "veckm_set_timing", "veckm_stage_times",
            "veckm_last_launch_count", "veckm_canvas_layout", "veckm_predict_batch",
            "veckm_encode_batch", "veckm_plan_create", "veckm_plan_launch",
@@ -101,6 +102,9 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_encode_noalloc.restype = C.c_int
     lib.veckm_predict.argtypes = ev
     lib.veckm_predict_host.argtypes = ev
+    lib.veckm_predict_host_async.argtypes = [P, P, P, P, i64, u32, P, i64, P,
+                                             C.POINTER(C.c_int64)]
+    lib.veckm_host_wait.argtypes = [P, i64]
     lib.veckm_set_mlp_mode.argtypes = [P, u32]
     lib.veckm_sync_status.argtypes = [P, P]
     lib.veckm_last_error.restype = C.c_char_p
@@ -138,6 +142,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_stream_destroy.argtypes = [P]
     lib.veckm_stream_destroy.restype = None
     for name in ("veckm_create", "veckm_encode", "veckm_predict", "veckm_predict_host",
+                 "veckm_predict_host_async", "veckm_host_wait",
                  "veckm_set_mlp_mode", "veckm_sync_status", "veckm_get_frequencies",
                  "veckm_set_timing", "veckm_stage_times", "veckm_last_launch_count",
                  "veckm_canvas_layout", "veckm_predict_batch", "veckm_encode_batch",
@@ -498,6 +503,35 @@ class Encoder:
         _check(lib().veckm_predict_host(self._h, hp(x), hp(y), hp(t), n, C.c_uint32(t_ref),
                                         hp(K), nK, hp(out), self._stream(stream)))
         return out
+
+    def predict_host_async(self, x, y, t, t_ref: int, K=None, out=None) -> Tuple[int, object]:
+        """Pipelined predict_host: returns (ticket, out) at once; out is filled
+        after host_wait(ticket).  Inputs should be pinned CPU tensors; they
+        are kept alive here until the call can no longer touch them."""
+        import torch
+        n = x.numel()
+        nK = n if K is None else K.numel()
+        if out is None:
+            out = torch.empty((nK, 2), dtype=torch.float32, pin_memory=True)
+        for a in (x, y, t, K, out):
+            assert a is None or (not a.is_cuda and a.is_contiguous())
+
+        def hp(a):
+            return None if a is None or a.numel() == 0 else C.c_void_p(a.data_ptr())
+        tk = C.c_int64(-1)
+        _check(lib().veckm_predict_host_async(self._h, hp(x), hp(y), hp(t), n, C.c_uint32(t_ref),
+                                              hp(K), nK, hp(out), C.byref(tk)))
+        # issuing ticket k retired ticket k - 2 inside the library
+        self._inflight = {k: v for k, v in getattr(self, "_inflight", {}).items()
+                          if k >= tk.value - 1}
+        self._inflight[tk.value] = (x, y, t, K, out)
+        return tk.value, out
+
+    def host_wait(self, ticket: int):
+        """Block until the pipelined call `ticket` has finished; raise its error."""
+        st = lib().veckm_host_wait(self._h, ticket)
+        getattr(self, "_inflight", {}).pop(ticket, None)
+        _check(st)
 
     def sync_status(self, stream=None):
         _check(lib().veckm_sync_status(self._h, self._stream(stream)))
