@@ -271,6 +271,7 @@ int tune_go(void *p, cudaStream_t s) {
 }
 
 veckm_status autotune(veckm_ctx *c, const Geometry &g, cudaStream_t s, int32_t *tuned) {
+  grids_dirty(c);  // the timing runs write both grids
   const int segs[] = {2, 3, 4, 6, 8, 12};
   const int wpbs[] = {1, 2, 3, 4};
   cudaEvent_t a = nullptr, b = nullptr;
@@ -432,6 +433,7 @@ veckm_status veckm_plan_create(veckm_ctx *c, const veckm_slice *sl, int32_t ns, 
 veckm_status veckm_plan_launch(veckm_plan *pl, void *stream) {
   if (!pl) return fail_msg(VECKM_EINVAL, "null plan");
   if (!pl->exec) return VECKM_OK;  // an empty batch
+  grids_dirty(pl->c);  // a replay leaves sums in both grids
   const cudaError_t e = cudaGraphLaunch(pl->exec, (cudaStream_t)stream);
   return e == cudaSuccess ? VECKM_OK : fail_cuda(e, "graph launch");
 }

@@ -27,6 +27,12 @@ struct veckm_ctx {
   float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
   uint16_t *W1h = nullptr;
   float4 *acc = nullptr, *hbuf = nullptr;
+  // Which of the two grids (0: acc, 1: hbuf; -1: neither) is known to hold
+  // zeros over its first zero_units float4, in stream order: the tensor-core
+  // head zeroes the dead row-pass grid for the next call's per-pixel sums,
+  // which then go there instead of clearing a grid first.
+  int zero_grid = -1;
+  int64_t zero_units = 0;
   int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
   int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
   // pixel-sorted event records (grown on demand)

@@ -951,9 +951,10 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 
 template <int DV>
 int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
+                const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear) {
   const int64_t P = (int64_t)g.W * g.H;
-  if (cudaMemsetAsync(acc, 0, (size_t)P * g.U * sizeof(float4), s) != cudaSuccess) return -1;
+  if (clear && cudaMemsetAsync(acc, 0, (size_t)P * g.U * sizeof(float4), s) != cudaSuccess)
+    return -1;
   if (n == 0) return 0;
   const int64_t warps = (n + kPixRecs - 1) / kPixRecs;
   const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
@@ -1106,8 +1107,8 @@ int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *
 }
 
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (pixsum_impl<DV>(g, tb, nsorted, rec, rpix, n, acc, s)));
+                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear) {
+  VECKM_DISPATCH_DV(g.U, (pixsum_impl<DV>(g, tb, nsorted, rec, rpix, n, acc, s, clear)));
 }
 
 int launch_pixsum_owned(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,

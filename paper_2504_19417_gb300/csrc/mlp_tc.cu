@@ -29,6 +29,10 @@
 // roles' previous use), so parity waits are unambiguous.  Every wait is
 // bounded: on time-out the kernel sets the error word and leaves.
 //
+// While they wait for accumulators, the epilogue warps can also zero a grid
+// buffer for the caller (the next call's per-pixel sums): each CTA clears one
+// contiguous share, a slice per tile, and on an early exit the rest of it.
+//
 // Requested events come either in pixel-sorted order (records of the
 // counting sort: consecutive rows mostly share a pooled row; producers
 // prefetch the following tile into L2) or by index (an explicit K list, or
@@ -153,7 +157,8 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
                  const int2 *__restrict__ rec, const int *__restrict__ rpix,
                  const int *__restrict__ nsorted, Geometry g, Tables tb,
                  const void *__restrict__ pooled_v, const int *__restrict__ ncnt, MLP mlp,
-                 float *__restrict__ flow, int *err) {
+                 float *__restrict__ flow, int *err, float4 *__restrict__ zero_buf,
+                 int64_t zero_units) {
   constexpr int U = 32 * DV;
   constexpr int IN = 4 * U;  // 2D, the MMA K extent
   constexpr int TILE_BYTES = kM * IN * 2;
@@ -418,6 +423,19 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
     constexpr uint32_t idesc_fp16 = make_idesc(1, kM, kN);
     const uint32_t idesc = fp16 ? idesc_fp16 : idesc_bf16;
     const uint32_t sA_a = smem_u32(sA), sB_a = smem_u32(sB);
+    // this CTA's share [z0, z1) of the buffer to zero, one slice per tile
+    int64_t z0 = 0, z1 = 0, zstep = 0;
+    if (zero_buf) {
+      const int64_t per_cta = (zero_units + gridDim.x - 1) / gridDim.x;
+      z0 = (int64_t)blockIdx.x * per_cta < zero_units ? (int64_t)blockIdx.x * per_cta : zero_units;
+      z1 = z0 + per_cta < zero_units ? z0 + per_cta : zero_units;
+      zstep = nlocal > 0 ? (z1 - z0 + nlocal - 1) / nlocal : 0;
+    }
+    auto zero_slice = [&](int c) {
+      const int64_t a = z0 + (int64_t)c * zstep, e = a + zstep < z1 ? a + zstep : z1;
+      for (int64_t u = a + row; u < e; u += kEpiWarps * 32) zero_buf[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    int zeroed = 0;  // slices this thread has cleared
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
       // full: the producers' tile and row metadata
@@ -495,7 +513,11 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       } else if (k <= -2) {
         *reinterpret_cast<float2 *>(flow + 2 * (size_t)(-2 - k)) = make_float2(0.f, 0.f);
       }
+      if (zero_buf) zero_slice(zeroed++);
     }
+    // the share is cleared in full even when a wait gave up
+    if (zero_buf)
+      while (zeroed < nlocal) zero_slice(zeroed++);
   }
   if (!ok && lane == 0) atomicOr(err, ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -515,7 +537,9 @@ template <int DV, bool HALF>
 int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                     const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                     const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
-                    cudaStream_t s, int ctas_req) {
+                    cudaStream_t s, int ctas_req, float4 *zero_buf, int64_t zero_units,
+                    bool *zeroed) {
+  if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
   const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (3 * kN + 2 * kM) +
@@ -531,9 +555,17 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (ctas_req > 0) per_sm = std::min(per_sm, ctas_req);
   const int64_t tiles = (nK + kM - 1) / kM;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm);
+  // zero the buffer only when every CTA has tiles enough to spread its share
+  // over (at most kZeroPerTile float4, 128 KB, per tile)
+  constexpr int64_t kZeroPerTile = 8192;
+  const int64_t min_local = tiles / grid;
+  const bool zero = zero_buf && zero_units > 0 &&
+                    (zero_units + grid - 1) / grid <= min_local * kZeroPerTile;
   kern<<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
-                                  err);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+                                  err, zero ? zero_buf : nullptr, zero ? zero_units : 0);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (zeroed) *zeroed = zero;
+  return 1;
 }
 
 }  // namespace
@@ -541,18 +573,22 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
-                      int *err, cudaStream_t s, const Tune &tn) {
+                      int *err, cudaStream_t s, const Tune &tn, float4 *zero_buf,
+                      int64_t zero_units, bool *zeroed) {
   const bool h = mlp.pooled_half != 0;
+#define VECKM_TC(DV_, H_)                                                                    \
+  predict_tc_impl<DV_, H_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, \
+                           tn.tc_ctas, zero_buf, zero_units, zeroed)
+  if (zeroed) *zeroed = false;
   switch (g.U / 32) {
     case 1:
-      return h ? predict_tc_impl<1, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas)
-               : predict_tc_impl<1, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas);
+      return h ? VECKM_TC(1, true) : VECKM_TC(1, false);
     case 2:
-      return h ? predict_tc_impl<2, true>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas)
-               : predict_tc_impl<2, false>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, tn.tc_ctas);
+      return h ? VECKM_TC(2, true) : VECKM_TC(2, false);
     default:
       return -1;  // 2D > 256 does not fit the operand tiles in shared memory
   }
+#undef VECKM_TC
 }
 
 }  // namespace veckm

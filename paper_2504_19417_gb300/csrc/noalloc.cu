@@ -81,6 +81,7 @@ extern "C" veckm_status veckm_encode_noalloc(veckm_ctx *ctx, const int16_t *d_x,
   int *rpix = reinterpret_cast<int *>(rec + kNoAllocMaxEvents);
 
   cudaStream_t s = (cudaStream_t)stream;
+  grids_dirty(ctx);  // both grids are written below
   const Geometry &g = c.g;
   const Events ev{d_x, d_y, d_t, n, t_ref_us, (uint32_t)c.t_span};
   const size_t P = (size_t)g.W * g.H;

@@ -236,6 +236,7 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   if (predict && g.D > 128 && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)))
     return fail_msg(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
   cudaStream_t cs = (cudaStream_t)stream;
+  grids_dirty(c);  // the push converts its sums into acc and pools through hbuf
   const uint32_t t_lo = t_hi_us >= (uint64_t)s->window ? t_hi_us - (uint32_t)s->window : 0u;
   const int DV = g.U / 32;
   auto apply = [&](int sign) {

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "ctx.h"
@@ -219,6 +220,7 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   launches += r;
   mark();
   if (direct) {
+    if (c->zero_grid == 0) c->zero_grid = -1;  // the owned sums write acc
     if ((r = launch_pixsum_owned(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s)) < 0)
       return cuda_fail(cudaGetLastError(), "pixel sum launch");
     launches += r;
@@ -236,11 +238,24 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     c->last_launches = launches;
     return VECKM_OK;
   }
-  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s)) < 0)
+  // The sums go to a grid known to be zero when there is one (the previous
+  // call's tensor-core head cleared it); otherwise acc is cleared first.  The
+  // row pass writes the other grid, the column pass writes back into the
+  // first, which the gather reads.  Graph captures always clear: a replay
+  // cannot know what ran before it.
+  const int64_t units = (int64_t)P * g.U;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "capture query");
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  const bool known_zero = !capturing && c->zero_grid >= 0 && c->zero_units >= units;
+  float4 *gsum = c->acc, *grow = c->hbuf;
+  if (known_zero && c->zero_grid == 1) std::swap(gsum, grow);
+  c->zero_grid = -1;
+  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, !known_zero)) < 0)
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
   mark();
-  if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, s, tn)) < 0)
+  if ((r = launch_pool_rows(g, tb, gsum, grow, s, tn)) < 0)
     return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   mark();
@@ -251,22 +266,28 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   // FP16 storage of the normalised pooled grid serves the tensor-core head only
   const bool half_grid = what == Out::Flow && (c->flags & VECKM_ACC_FP16);
   if (half_grid)
-    r = launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, s, tn);
+    r = launch_pool_cols_half(g, tb, grow, c->ncnt, gsum, s, tn);
   else
-    r = launch_pool_cols(g, tb, c->hbuf, c->acc, s, tn);
+    r = launch_pool_cols(g, tb, grow, gsum, s, tn);
   if (r < 0) return cuda_fail(cudaGetLastError(), "pooling (columns) launch");
   launches += r;
   mark();
   if (what == Out::Emb) {
-    r = launch_gather_emb(ev, K, nK, g, tb, c->acc, c->ncnt, out, c->err, s);
+    r = launch_gather_emb(ev, K, nK, g, tb, gsum, c->ncnt, out, c->err, s);
   } else if (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)) {
     MLP m = c->mlp();
     m.pooled_half = half_grid ? 1 : 0;
+    bool zeroed = false;
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
-                          c->off + P, g, tb, c->acc, c->ncnt, m, out, c->err, s, tn);
+                          c->off + P, g, tb, gsum, c->ncnt, m, out, c->err, s, tn,
+                          capturing ? nullptr : grow, units, &zeroed);
+    if (r >= 0 && zeroed) {
+      c->zero_grid = grow == c->acc ? 0 : 1;
+      c->zero_units = units;
+    }
   } else {
     r = launch_predict_fp32(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
-                            c->off + P, g, tb, c->acc, c->ncnt, c->mlp(), out, c->err, s);
+                            c->off + P, g, tb, gsum, c->ncnt, c->mlp(), out, c->err, s);
     if (r == -2) return fail(VECKM_EUNSUPPORTED, "FP32 perceptron needs 2D*128 floats of shared memory; D=%d is too large", g.D);
   }
   if (r < 0) return cuda_fail(cudaGetLastError(), "gather launch");
@@ -634,6 +655,10 @@ bool ctx_view(const veckm_ctx *c, CtxView *v) {
 }
 
 veckm_status report(veckm_status st, const char *msg) { return fail(st, "%s", msg); }
+
+void grids_dirty(veckm_ctx *c) {
+  if (c) c->zero_grid = -1;
+}
 
 veckm_status fail_msg(veckm_status st, const char *fmt, ...) {
   va_list ap;

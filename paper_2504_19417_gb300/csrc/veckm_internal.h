@@ -67,9 +67,10 @@ int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur
                 cudaStream_t s);
 int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
                  cudaStream_t s);
-// Clears acc, then sums the *nsorted pixel-sorted records (n bounds it).
+// Clears acc (unless the caller knows it is zero: clear = false), then sums
+// the *nsorted pixel-sorted records (n bounds it).
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s);
+                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear = true);
 // Blocks of `threads` threads with `smem` dynamic bytes that fit on one SM.
 int blocks_per_sm(const void *func, int threads, size_t smem);
 // Pooling: row pass acc -> hbuf, column pass hbuf -> acc, window counts.
@@ -96,7 +97,12 @@ int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const in
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
-                      int *err, cudaStream_t s, const Tune &tn = Tune{});
+                      int *err, cudaStream_t s, const Tune &tn = Tune{},
+                      float4 *zero_buf = nullptr, int64_t zero_units = 0,
+                      bool *zeroed = nullptr);
+// Forget which grid of the context is known to be zero (for paths that write
+// the grids outside the dense pipeline).
+void grids_dirty(veckm_ctx *c);
 
 // Direct window form: per-pixel sums written once per occupied pixel (no
 // clear), then one warp per requested event summing its window (mlp == NULL:

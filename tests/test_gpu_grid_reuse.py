@@ -1,0 +1,111 @@
+"""GPU tests of grid reuse between calls: the tensor-core head zeroes the
+row-pass grid for the next call's per-pixel sums, so successive dense calls
+alternate between the context's two grids and skip the clear.  Every path
+that writes a grid otherwise (the FP32 and embedding gathers, the direct
+window form, streams, captured plans, the autotuner, calls too small to
+spread the clearing) must leave the next call correct.  Each result is
+checked against the FP64 oracle (Eq. 16 and Eq. 6); slices alternate between
+dense and sparse so that a stale sum left in a grid would show."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_19417_gb300 import synth
+from paper_2504_19417_gb300 import veckm as vk
+from tests.common import EMB_TOL_FP32, emb_rel_err, make, to_dev, within_half_bound
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+W, H, D = 160, 120, 64
+
+
+def _sl(seed, n):
+    return synth.event_slice(W, H, n, 20_000, n_edges=3 + seed % 5, frac_noise=0.1, seed=seed)
+
+
+def _emb_ref(sl, TXY, K=None):
+    T, X, Y = TXY
+    return oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, W, H, D, 10, 10, 16_000.0, T, X, Y,
+                                K=K)[0]
+
+
+def _check_predict(enc, sl, TXY, w, mode, K=None):
+    x, y, t = to_dev(sl)
+    Kd = None if K is None else torch.from_numpy(K).cuda()
+    f = enc.predict(x, y, t, sl.t_ref, K=Kd).cpu().numpy()
+    e = _emb_ref(sl, TXY, K)
+    r = within_half_bound(f, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, mode)
+    assert r <= 1.0, r
+
+
+@pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_FP16 | vk.ACC_FP16, vk.MLP_BF16])
+def test_successive_predicts_alternate_grids(mode):
+    sizes = [40_000, 12_000, 30_000, 12_000, 25_000]
+    sls = [_sl(200 + i, n) for i, n in enumerate(sizes)]
+    enc, TXY, w = make(sls[0], D, mode=mode, t_span_us=20_000)
+    for sl in sls:
+        _check_predict(enc, sl, TXY, w, mode)
+    enc.sync_status()
+    enc.close()
+
+
+def test_every_path_between_predicts_leaves_the_next_one_correct():
+    mode = vk.MLP_FP16
+    enc, TXY, w = make(_sl(300, 10), D, mode=mode, t_span_us=20_000)
+    dense, sparse = _sl(301, 40_000), _sl(302, 12_000)
+
+    def predict_pair():
+        _check_predict(enc, dense, TXY, w, mode)
+        _check_predict(enc, sparse, TXY, w, mode)
+
+    predict_pair()
+    # the embedding gather (no clearing) on the cleared grid
+    x, y, t = to_dev(dense)
+    emb = enc.encode(x, y, t, dense.t_ref).cpu().numpy()
+    assert emb_rel_err(emb, _emb_ref(dense, TXY)).max() <= EMB_TOL_FP32
+    predict_pair()
+    # the direct window form writes only occupied pixels of the first grid
+    enc.set_path(vk.PATH_DIRECT)
+    K = np.arange(0, sparse.n, 97, dtype=np.int64)
+    x, y, t = to_dev(sparse)
+    f = enc.predict(x, y, t, sparse.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
+    e = _emb_ref(sparse, TXY, K)
+    assert within_half_bound(f, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, vk.MLP_FP32) <= 1.0
+    enc.set_path(vk.PATH_AUTO)
+    predict_pair()
+    # the FP32 head (no clearing)
+    enc.set_mlp_mode(vk.MLP_FP32)
+    _check_predict(enc, dense, TXY, w, vk.MLP_FP32)
+    enc.set_mlp_mode(mode)
+    predict_pair()
+    # a call with too few requests to spread the clearing over, then full calls
+    _check_predict(enc, dense, TXY, w, mode, K=np.arange(0, dense.n, 4001, dtype=np.int64))
+    predict_pair()
+    # a stream push converts its sums into the grids
+    st = vk.Stream(enc, 20_000, 50_000)
+    x, y, t = to_dev(sparse)
+    st.push(x, y, t, int(sparse.t.max()) + 1, predict=False)
+    st.close()
+    predict_pair()
+    # a captured plan replays its own clear, and the autotuner writes both grids
+    plan = enc.plan([vk.Slice(x, y, t, sparse.t_ref, W, H)])
+    got = plan.launch().cpu().numpy()
+    e = _emb_ref(sparse, TXY)
+    assert within_half_bound(got, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, mode) <= 1.0
+    plan.close()
+    predict_pair()
+    enc.autotune(W, H)
+    predict_pair()
+    # pipelined host calls run on the context's own streams
+    tk, out = enc.predict_host_async(torch.from_numpy(dense.x).pin_memory(),
+                                     torch.from_numpy(dense.y).pin_memory(),
+                                     torch.from_numpy(dense.t.view(np.int32)).pin_memory(),
+                                     dense.t_ref)
+    enc.host_wait(tk)
+    e = _emb_ref(dense, TXY)
+    assert within_half_bound(out.numpy(), oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, mode) <= 1.0
+    predict_pair()
+    enc.sync_status()
+    enc.close()

@@ -52,6 +52,27 @@ def test_noalloc_encode_matches_encode_on_consecutive_calls():
     enc.sync_status()
 
 
+def test_predict_after_noalloc_encode():
+    # a tensor-core predict zeroes one grid for the next call; the no-alloc
+    # encode in between writes both grids, and the predict after it must
+    # not take either for zero
+    import oracle
+    from tests.common import within_half_bound
+    sl = synth.event_slice(160, 120, 30_000, 20_000, n_edges=6, seed=315)
+    sparse = synth.event_slice(160, 120, 12_000, 20_000, n_edges=3, seed=316)
+    enc, (T, X, Y), w = make(sl, 64, mode=vk.MLP_FP16, t_span_us=20_000)
+    x, y, t = to_dev(sl)
+    enc.predict(x, y, t, sl.t_ref)
+    out = torch.empty((sl.n, 128), dtype=torch.float32, device="cuda")
+    assert _noalloc(enc, x, y, t, sl.t_ref, None, sl.n, out) == vk.VECKM_OK
+    xs, ys, ts = to_dev(sparse)
+    f = enc.predict(xs, ys, ts, sparse.t_ref).cpu().numpy()
+    e = oracle.encode_pooled(sparse.x, sparse.y, sparse.t, sparse.t_ref, 160, 120, 64, 10, 10,
+                             16_000.0, T, X, Y)[0]
+    assert within_half_bound(f, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, vk.MLP_FP16) <= 1.0
+    enc.sync_status()
+
+
 def test_noalloc_encode_rejects_more_events_than_its_array():
     sl = synth.event_slice(64, 48, 100, 1_000, seed=2)
     enc, _, _ = make(sl, 64)
