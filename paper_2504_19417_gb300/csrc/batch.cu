@@ -331,11 +331,17 @@ bool tuned_for(const veckm_ctx *c, const Geometry &g) {
 
 using namespace veckm;
 
+// A plan holds one graph that clears the grid its sums go to, or, when the
+// captured tensor-core head zeroes the other grid, two graphs with the grids'
+// roles swapped: a launch replays the one whose sums go to the grid the
+// context knows to be zero (clearing acc first when neither is).
 struct veckm_plan {
   veckm_ctx *c = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  void *h_tab = nullptr;  // pinned slice table read by the graph's copy node
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  bool pingpong = false;
+  int64_t units = 0;      // float4 of each grid the canvas uses
+  void *h_tab = nullptr;  // pinned slice table read by the graphs' copy nodes
   int kernels = 0;
 };
 
@@ -395,32 +401,56 @@ veckm_status veckm_plan_create(veckm_ctx *c, const veckm_slice *sl, int32_t ns, 
     if (e != cudaSuccess) st = fail_cuda(e, "plan slice table");
     else std::memcpy(pl->h_tab, p.tab.data(), bytes);
   }
-  if (st == VECKM_OK && p.N > 0) {
+  // capture one graph with the sums in grid `grid` (-1: cleared in the graph)
+  auto capture = [&](int grid, int slot) -> veckm_status {
     const bool timing = c->timing;
     c->timing = false;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) {
-      st = fail_cuda(e, "stream capture");
+    c->capture_grid = grid;
+    c->capture_zeroed = false;
+    veckm_status r = VECKM_OK;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) {
+      r = fail_cuda(ce, "stream capture");
     } else {
-      e = cudaMemcpyAsync(c->slice_tab, pl->h_tab, bytes, cudaMemcpyHostToDevice, cs);
-      st = e == cudaSuccess ? run_canvas(c, p, d_out, predict != 0, cs)
-                            : fail_cuda(e, "slice table copy");
+      ce = cudaMemcpyAsync(c->slice_tab, pl->h_tab, bytes, cudaMemcpyHostToDevice, cs);
+      r = ce == cudaSuccess ? run_canvas(c, p, d_out, predict != 0, cs)
+                            : fail_cuda(ce, "slice table copy");
       cudaGraph_t graph = nullptr;
       const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
-      pl->graph = graph;
-      if (st == VECKM_OK && ee != cudaSuccess) st = fail_cuda(ee, "stream capture");
+      pl->graph[slot] = graph;
+      if (r == VECKM_OK && ee != cudaSuccess) r = fail_cuda(ee, "stream capture");
     }
+    c->capture_grid = -1;
     c->timing = timing;
     pl->kernels = c->last_launches;
-    if (st == VECKM_OK) {
-      e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
-      if (e != cudaSuccess) st = fail_cuda(e, "graph instantiation");
+    if (r == VECKM_OK) {
+      ce = cudaGraphInstantiate(&pl->exec[slot], pl->graph[slot], 0);
+      if (ce != cudaSuccess) r = fail_cuda(ce, "graph instantiation");
+    }
+    return r;
+  };
+  if (st == VECKM_OK && p.N > 0) {
+    st = capture(0, 0);
+    if (st == VECKM_OK && c->capture_zeroed) {
+      pl->pingpong = true;
+      pl->units = c->capture_units;
+      st = capture(1, 1);
+      if (st == VECKM_OK && !c->capture_zeroed) st = fail_msg(VECKM_ECUDA, "plan graphs disagree");
+    } else if (st == VECKM_OK) {
+      // the head does not zero a grid here: one graph that clears its own
+      cudaGraphExecDestroy(pl->exec[0]);
+      cudaGraphDestroy(pl->graph[0]);
+      pl->exec[0] = nullptr;
+      pl->graph[0] = nullptr;
+      st = capture(-1, 0);
     }
   }
   if (cs) cudaStreamDestroy(cs);
   if (st != VECKM_OK) {
-    if (pl->exec) cudaGraphExecDestroy(pl->exec);
-    if (pl->graph) cudaGraphDestroy(pl->graph);
+    for (int k = 0; k < 2; ++k) {
+      if (pl->exec[k]) cudaGraphExecDestroy(pl->exec[k]);
+      if (pl->graph[k]) cudaGraphDestroy(pl->graph[k]);
+    }
     if (pl->h_tab) cudaFreeHost(pl->h_tab);
     delete pl;
     return st;
@@ -432,21 +462,38 @@ veckm_status veckm_plan_create(veckm_ctx *c, const veckm_slice *sl, int32_t ns, 
 
 veckm_status veckm_plan_launch(veckm_plan *pl, void *stream) {
   if (!pl) return fail_msg(VECKM_EINVAL, "null plan");
-  if (!pl->exec) return VECKM_OK;  // an empty batch
-  grids_dirty(pl->c);  // a replay leaves sums in both grids
-  const cudaError_t e = cudaGraphLaunch(pl->exec, (cudaStream_t)stream);
-  return e == cudaSuccess ? VECKM_OK : fail_cuda(e, "graph launch");
+  if (!pl->exec[0]) return VECKM_OK;  // an empty batch
+  veckm_ctx *c = pl->c;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!pl->pingpong) {
+    grids_dirty(c);  // a replay leaves sums in both grids
+    const cudaError_t e = cudaGraphLaunch(pl->exec[0], s);
+    return e == cudaSuccess ? VECKM_OK : fail_cuda(e, "graph launch");
+  }
+  int which = c->zero_grid >= 0 && c->zero_units >= pl->units ? c->zero_grid : -1;
+  grids_dirty(c);
+  cudaError_t e = cudaSuccess;
+  if (which < 0) {
+    e = cudaMemsetAsync(c->acc, 0, (size_t)pl->units * sizeof(float4), s);
+    which = 0;
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(pl->exec[which], s);
+  if (e != cudaSuccess) return fail_cuda(e, "graph launch");
+  // the replay's head zeroed the grid its row pass wrote
+  c->zero_grid = which == 0 ? 1 : 0;
+  c->zero_units = pl->units;
+  return VECKM_OK;
 }
 
 int veckm_plan_kernel_count(const veckm_plan *pl) { return pl ? pl->kernels : 0; }
 
 void veckm_plan_destroy(veckm_plan *pl) {
   if (!pl) return;
-  if (pl->exec) {
-    cudaDeviceSynchronize();  // replays still in flight read the pinned table
-    cudaGraphExecDestroy(pl->exec);
+  if (pl->exec[0]) cudaDeviceSynchronize();  // replays still in flight read the pinned table
+  for (int k = 0; k < 2; ++k) {
+    if (pl->exec[k]) cudaGraphExecDestroy(pl->exec[k]);
+    if (pl->graph[k]) cudaGraphDestroy(pl->graph[k]);
   }
-  if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->h_tab) cudaFreeHost(pl->h_tab);
   if (pl->c) pl->c->live_plans -= 1;
   delete pl;

@@ -33,6 +33,12 @@ struct veckm_ctx {
   // which then go there instead of clearing a grid first.
   int zero_grid = -1;
   int64_t zero_units = 0;
+  // While a plan is captured: the grid (0 or 1) its sums go to without a
+  // clear, the head zeroing the other one (-1: clear acc inside the graph);
+  // and whether the captured head does zero it, over how many float4.
+  int capture_grid = -1;
+  bool capture_zeroed = false;
+  int64_t capture_units = 0;
   int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
   int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
   // pixel-sorted event records (grown on demand)

@@ -241,16 +241,21 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   // The sums go to a grid known to be zero when there is one (the previous
   // call's tensor-core head cleared it); otherwise acc is cleared first.  The
   // row pass writes the other grid, the column pass writes back into the
-  // first, which the gather reads.  Graph captures always clear: a replay
-  // cannot know what ran before it.
+  // first, which the gather reads.  A graph capture cannot know what runs
+  // before a replay: it clears, unless the plan capturing it picks the grid
+  // (capture_grid) and chooses between its two graphs at each launch.
   const int64_t units = (int64_t)P * g.U;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "capture query");
   const bool capturing = cap != cudaStreamCaptureStatusNone;
-  const bool known_zero = !capturing && c->zero_grid >= 0 && c->zero_units >= units;
+  const int zgrid = capturing ? c->capture_grid
+                              : (c->zero_grid >= 0 && c->zero_units >= units ? c->zero_grid : -1);
+  const bool known_zero = zgrid >= 0;
+  const bool may_zero = !capturing || c->capture_grid >= 0;
   float4 *gsum = c->acc, *grow = c->hbuf;
-  if (known_zero && c->zero_grid == 1) std::swap(gsum, grow);
+  if (zgrid == 1) std::swap(gsum, grow);
   c->zero_grid = -1;
+  c->capture_zeroed = false;
   if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, !known_zero)) < 0)
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
@@ -280,10 +285,14 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     bool zeroed = false;
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
                           c->off + P, g, tb, gsum, c->ncnt, m, out, c->err, s, tn,
-                          capturing ? nullptr : grow, units, &zeroed);
-    if (r >= 0 && zeroed) {
+                          may_zero ? grow : nullptr, units, &zeroed);
+    if (r >= 0 && zeroed && !capturing) {
       c->zero_grid = grow == c->acc ? 0 : 1;
       c->zero_units = units;
+    }
+    if (r >= 0 && zeroed && capturing) {
+      c->capture_zeroed = true;
+      c->capture_units = units;
     }
   } else {
     r = launch_predict_fp32(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,

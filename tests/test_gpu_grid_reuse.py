@@ -89,11 +89,20 @@ def test_every_path_between_predicts_leaves_the_next_one_correct():
     st.push(x, y, t, int(sparse.t.max()) + 1, predict=False)
     st.close()
     predict_pair()
-    # a captured plan replays its own clear, and the autotuner writes both grids
+    # a captured plan holds two graphs with the grids' roles swapped and
+    # replays the one whose sums go to the zeroed grid: back-to-back
+    # replays, replays between predicts, and after paths that dirty both
     plan = enc.plan([vk.Slice(x, y, t, sparse.t_ref, W, H)])
-    got = plan.launch().cpu().numpy()
     e = _emb_ref(sparse, TXY)
-    assert within_half_bound(got, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, mode) <= 1.0
+    fref = oracle.mlp(e, w.W1, w.b1, w.W2, w.b2)
+    for step in range(6):
+        got = plan.launch().cpu().numpy()
+        assert within_half_bound(got, fref, e, w, mode) <= 1.0, step
+        if step == 2:
+            predict_pair()
+        if step == 4:
+            x2, y2, t2 = to_dev(dense)
+            enc.encode(x2, y2, t2, dense.t_ref)
     plan.close()
     predict_pair()
     enc.autotune(W, H)
