@@ -39,6 +39,10 @@ struct veckm_ctx {
   int capture_grid = -1;
   bool capture_zeroed = false;
   int64_t capture_units = 0;
+  // Side stream for the window counts of the dense path (they need only the
+  // histogram), forked from and joined back to the caller's stream.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
   int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
   // pixel-sorted event records (grown on demand)

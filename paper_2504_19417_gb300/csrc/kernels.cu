@@ -17,7 +17,7 @@
 //                   sum_q A[q] exp(i (q-p).w) = conj(phi(p)) sum_q A[q] phi(q)
 //                 with phi(q) = exp(i q.w), this equals the window sum with
 //                 the precomputed spatial factors of Eq. 16.
-//   6. k_count_*  window counts n (Eq. 17), exact integer box sums.
+//   6. k_count_box window counts n (Eq. 17), exact integer box sums (one tiled pass).
 //   7. gather     pooled[p] * conj(exp(i t T/dt)) / n (Eq. 16), fused with the
 //                 perceptron (mlp_tc.cu, or the FP32 kernel below).
 //
@@ -507,25 +507,41 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
 }
 
 // 6. window counts (Eq. 17): exact integer box sums, rows then columns.
-__global__ void k_count_rows(const int *__restrict__ cnt, int *__restrict__ out, int W, int H,
-                             int dx) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)W * H) return;
-  const int y = (int)(i / W), x = (int)(i % W);
-  const int *row = cnt + (size_t)y * W;
-  int s = 0;
-  for (int a = max(0, x - dx); a <= min(W - 1, x + dx); ++a) s += row[a];
-  out[i] = s;
-}
+// Window counts in one pass: a block stages a kCountTile x kCountTile output
+// tile and its halo (zeros outside the sensor, which equals clipping the
+// window there) in shared memory, sums rows of 2dx+1, then columns of 2dy+1.
+constexpr int kCountTile = 32;
 
-__global__ void k_count_cols(const int *__restrict__ rows, int *__restrict__ out, int W, int H,
-                             int dy) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)W * H) return;
-  const int y = (int)(i / W), x = (int)(i % W);
-  int s = 0;
-  for (int b = max(0, y - dy); b <= min(H - 1, y + dy); ++b) s += rows[(size_t)b * W + x];
-  out[i] = s;
+__global__ void __launch_bounds__(256) k_count_box(const int *__restrict__ cnt,
+                                                   int *__restrict__ out, int W, int H, int dx,
+                                                   int dy) {
+  extern __shared__ int csm[];
+  const int iw = kCountTile + 2 * dx, ih = kCountTile + 2 * dy;
+  int *in = csm;             // [ih][iw] counts
+  int *rs = csm + iw * ih;   // [ih][kCountTile] row sums
+  const int x0 = blockIdx.x * kCountTile, y0 = blockIdx.y * kCountTile;
+  for (int i = threadIdx.x; i < iw * ih; i += blockDim.x) {
+    const int gy = y0 - dy + i / iw, gx = x0 - dx + i % iw;
+    in[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? __ldg(cnt + (size_t)gy * W + gx) : 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ih * kCountTile; i += blockDim.x) {
+    const int r = i / kCountTile, c = i % kCountTile;
+    const int *p = in + r * iw + c;
+    int sum = 0;
+    for (int a = 0; a <= 2 * dx; ++a) sum += p[a];
+    rs[i] = sum;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kCountTile * kCountTile; i += blockDim.x) {
+    const int r = i / kCountTile, c = i % kCountTile;
+    const int gy = y0 + r, gx = x0 + c;
+    if (gy >= H || gx >= W) continue;
+    const int *p = rs + r * kCountTile + c;
+    int sum = 0;
+    for (int b = 0; b <= 2 * dy; ++b) sum += p[b * kCountTile];
+    out[(size_t)gy * W + gx] = sum;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1146,11 +1162,14 @@ int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbu
 }
 
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s) {
-  const int64_t P = (int64_t)g.W * g.H;
-  const int grid = (int)((P + 255) / 256);
-  k_count_rows<<<grid, 256, 0, s>>>(cnt, cnt_tmp, g.W, g.H, g.dx);
-  k_count_cols<<<grid, 256, 0, s>>>(cnt_tmp, ncnt, g.W, g.H, g.dy);
-  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+  (void)cnt_tmp;  // the tiled pass keeps its row sums in shared memory
+  const size_t iw = kCountTile + 2 * (size_t)g.dx, ih = kCountTile + 2 * (size_t)g.dy;
+  const size_t sm = (iw * ih + ih * kCountTile) * sizeof(int);
+  if (set_smem(k_count_box, sm) != cudaSuccess) return -1;
+  const dim3 grid((unsigned)((g.W + kCountTile - 1) / kCountTile),
+                  (unsigned)((g.H + kCountTile - 1) / kCountTile));
+  k_count_box<<<grid, 256, sm, s>>>(cnt, ncnt, g.W, g.H, g.dx, g.dy);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,

@@ -113,6 +113,9 @@ void free_all(veckm_ctx *c) {
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->h_slice_tab) cudaFreeHost(c->h_slice_tab);
   if (c->tab_copied) cudaEventDestroy(c->tab_copied);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   for (auto &v : c->pending)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -215,6 +218,29 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s)) < 0)
     return cuda_fail(cudaGetLastError(), "scan launch");
   launches += r;
+  // The window counts need only the histogram: on the dense path they run on
+  // the side stream, under the placement, pixel sums and row pass, and join
+  // before the column pass (on every return once forked).
+  struct Join {
+    veckm_ctx *c;
+    cudaStream_t s;
+    bool armed = false;
+    void wait() {
+      if (armed) cudaStreamWaitEvent(s, c->ev_join, 0);
+      armed = false;
+    }
+    ~Join() { wait(); }
+  } join{c, s};
+  if (!direct) {
+    cudaError_t fe = cudaEventRecord(c->ev_fork, s);
+    if (fe == cudaSuccess) fe = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (fe != cudaSuccess) return cuda_fail(fe, "forking the window counts");
+    r = launch_counts(g, c->cnt, c->cnt_tmp, c->ncnt, c->side);
+    fe = cudaEventRecord(c->ev_join, c->side);
+    join.armed = true;
+    if (r < 0 || fe != cudaSuccess) return cuda_fail(cudaGetLastError(), "window count launch");
+    launches += r;
+  }
   if ((r = launch_place(ev, g, c->cur, c->rec, c->rpix, s)) < 0)
     return cuda_fail(cudaGetLastError(), "placement launch");
   launches += r;
@@ -264,9 +290,7 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   mark();
-  if ((r = launch_counts(g, c->cnt, c->cnt_tmp, c->ncnt, s)) < 0)
-    return cuda_fail(cudaGetLastError(), "window count launch");
-  launches += r;
+  join.wait();  // the window counts (side stream)
   mark();
   // FP16 storage of the normalised pooled grid serves the tensor-core head only
   const bool half_grid = what == Out::Flow && (c->flags & VECKM_ACC_FP16);
@@ -432,6 +456,9 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   do {                                  \
     if (e == cudaSuccess) e = (expr);   \
   } while (0)
+  VK_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  VK_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  VK_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   VK_TRY(dalloc(&c->tx, ((size_t)g.W + cfg->dx) * g.U));
   VK_TRY(dalloc(&c->sx, (size_t)g.U));
   VK_TRY(dalloc(&c->sy, (size_t)g.U));
