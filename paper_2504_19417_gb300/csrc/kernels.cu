@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__res
 // 4. per-pixel phase sums PixelEmbed[p] = sum over the pixel's records of
 // exp(i t T/dt), into an accumulator cleared beforehand (empty pixels stay
 // zero).  Work is balanced by records: warp c takes records
-// [c*kPixRecs, (c+1)*kPixRecs) in pixel-sorted order, streams them in chunks
-// of 32 (t and pixel), and writes each pixel's sum when the pixel changes -
+// [c*recs, (c+1)*recs) in pixel-sorted order, streams them in groups of 32
+// (t and pixel, the next group loading while one is summed), and writes each
+// pixel's sum when the pixel changes -
 // a plain store for pixels that lie wholly inside its range, a vector
 // reduction for the first and last pixel, which may continue in a
 // neighbouring warp's range.
@@ -275,16 +276,16 @@ template <int DV>
 __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int *__restrict__ nsorted,
                                                 const int2 *__restrict__ rec,
                                                 const int *__restrict__ rpix,
-                                                float4 *__restrict__ acc) {
+                                                float4 *__restrict__ acc, int recs) {
   constexpr int U = 32 * DV;
   const int lane = threadIdx.x & 31;
   const int64_t ns = *nsorted;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   uint2 w[DV][2];
   load_freqs<DV>(tb.wt, lane, w);
-  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kPixRecs;
-       r0 < ns; r0 += nw * kPixRecs) {
-    const int64_t r1 = r0 + kPixRecs < ns ? r0 + kPixRecs : ns;
+  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * recs;
+       r0 < ns; r0 += nw * recs) {
+    const int64_t r1 = r0 + recs < ns ? r0 + recs : ns;
     int sp = -1;        // pixel of the running sum
     bool first = true;  // the running pixel is the first of this range
     float4 s[DV];
@@ -300,10 +301,17 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
           dst[32 * v] = s[v];
       }
     };
+    // records of the next group of 32 load while this group is summed
+    uint32_t tn = lane < r1 - r0 ? (uint32_t)__ldg(&rec[r0 + lane].x) : 0u;
+    int pn = lane < r1 - r0 ? __ldg(rpix + r0 + lane) : 0;
     for (int64_t c = r0; c < r1; c += 32) {
       const int m = (int)(r1 - c < 32 ? r1 - c : 32);
-      const uint32_t tl = lane < m ? (uint32_t)__ldg(&rec[c + lane].x) : 0u;
-      const int pl = lane < m ? __ldg(rpix + c + lane) : 0;
+      const uint32_t tl = tn;
+      const int pl = pn;
+      if (c + 32 < r1) {
+        tn = lane < r1 - c - 32 ? (uint32_t)__ldg(&rec[c + 32 + lane].x) : 0u;
+        pn = lane < r1 - c - 32 ? __ldg(rpix + c + 32 + lane) : 0;
+      }
 #pragma unroll 4
       for (int j = 0; j < m; ++j) {
         const int pj = __shfl_sync(kFull, pl, j);
@@ -972,9 +980,12 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
   if (clear && cudaMemsetAsync(acc, 0, (size_t)P * g.U * sizeof(float4), s) != cudaSuccess)
     return -1;
   if (n == 0) return 0;
-  const int64_t warps = (n + kPixRecs - 1) / kPixRecs;
+  // 128 records per warp: measured on GB300 against 64 to 256 and against
+  // one wave of longer ranges (the window counts share the SMs meanwhile)
+  const int64_t recs = kPixRecs;
+  const int64_t warps = (n + recs - 1) / recs;
   const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
-  k_pixsum<DV><<<grid, 256, 0, s>>>(g, tb, nsorted, rec, rpix, acc);
+  k_pixsum<DV><<<grid, 256, 0, s>>>(g, tb, nsorted, rec, rpix, acc, (int)recs);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
