@@ -50,6 +50,7 @@ struct veckm_ctx {
   int *rpix = nullptr;
   int64_t rec_cap = 0;
   std::vector<float> hW1;  // host copy (re-encoding on precision switch)
+  std::vector<float> hb1, hW2, hb2;  // host copies (kernel parameters)
   // staging for the host-buffer entry point
   void *st_buf = nullptr;
   size_t st_cap = 0;
@@ -93,7 +94,8 @@ struct veckm_ctx {
     return veckm::Tune{};
   }
   veckm::MLP mlp() const {
-    return veckm::MLP{W1, W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0};
+    return veckm::MLP{W1,     W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0,
+                      hb1.data(), hW2.data(), hb2.data()};
   }
 };
 

@@ -33,6 +33,10 @@
 // buffer for the caller (the next call's per-pixel sums): each CTA clears one
 // contiguous share, a slice per tile, and on an early exit the rest of it.
 //
+// b1, W2 and b2 reach the epilogue as a kernel parameter: read through the
+// constant cache, they take no slots of the shared-memory pipe, which the
+// producers' loads and tile stores and the MMAs' operand reads share.
+//
 // Requested events come either in pixel-sorted order (records of the
 // counting sort: consecutive rows mostly share a pooled row; producers
 // prefetch the following tile into L2) or by index (an explicit K list, or
@@ -59,6 +63,13 @@ constexpr int kMmaWarp = 0;  // epilogue warp 0 also issues the MMAs
 constexpr int kThreads = 32 * (kEpiWarps + kProdWarps);
 constexpr int kRowsPerWarp = kM / kProdWarps;
 constexpr int kTmemCols = 2 * kN;  // two accumulators
+
+// Second-layer weights and first-layer bias, by value.
+struct __align__(16) EpiParams {
+  float b1[kN];
+  float w2[2][kN];
+  float b2[2];
+};
 // Output row codes (event counts are below 2^30): k >= 0 writes the flow of
 // row k; -1 writes nothing; k <= -2 writes zeros to row -2 - k (an invalid
 // event or index).
@@ -158,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
                  const int *__restrict__ nsorted, Geometry g, Tables tb,
                  const void *__restrict__ pooled_v, const int *__restrict__ ncnt, MLP mlp,
                  float *__restrict__ flow, int *err, float4 *__restrict__ zero_buf,
-                 int64_t zero_units) {
+                 int64_t zero_units, const __grid_constant__ EpiParams ep) {
   constexpr int U = 32 * DV;
   constexpr int IN = 4 * U;  // 2D, the MMA K extent
   constexpr int TILE_BYTES = kM * IN * 2;
@@ -166,9 +177,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;                            // 2 x [128 x IN] half, SW128
   uint8_t *sB = smem + 2 * TILE_BYTES;           // [128 x IN] half (W1), SW128
-  float *sB1 = reinterpret_cast<float *>(sB + TILE_BYTES);    // [128]
-  float *sW2 = sB1 + kN;                                       // [2][128]
-  float *sInv = sW2 + 2 * kN;                                  // [2][128] 1 / window count
+  float *sInv = reinterpret_cast<float *>(sB + TILE_BYTES);   // [2][128] 1 / window count
   int *sK = reinterpret_cast<int *>(sInv + 2 * kM);            // [2][128] output row codes
   uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 2 * kM);  // full[2], done[2], empty[2]
   int2 *sMeta = reinterpret_cast<int2 *>(bars + 6);             // [8 warps][2][16]
@@ -177,15 +186,10 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int fp16 = mlp.half_kind;
 
-  {  // W1 (already in SW128 order), b1, W2
+  {  // W1 (already in SW128 order)
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
     uint4 *dst = reinterpret_cast<uint4 *>(sB);
     for (int i = tid; i < TILE_BYTES / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-    for (int i = tid; i < kN; i += blockDim.x) {
-      sB1[i] = mlp.b1[i];
-      sW2[i] = mlp.W2[i];
-      sW2[kN + i] = mlp.W2[kN + i];
-    }
   }
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int b) { return bar0 + 8u * b; };
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
     // ------------------------------------------------------------ epilogue
     // (warp kMmaWarp issues each tile's MMAs first)
     const int row = warp * 32 + lane;  // TMEM lane = tile row
-    const float b20 = mlp.b2[0], b21 = mlp.b2[1];
+    const float b20 = ep.b2[0], b21 = ep.b2[1];
     constexpr uint32_t idesc_bf16 = make_idesc(0, kM, kN);
     constexpr uint32_t idesc_fp16 = make_idesc(1, kM, kN);
     const uint32_t idesc = fp16 ? idesc_fp16 : idesc_bf16;
@@ -491,9 +495,9 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
         tmem_ld16(base + c0, h);
 #pragma unroll
         for (int j = 0; j < 16; j += 4) {
-          const float4 bb = *reinterpret_cast<const float4 *>(sB1 + c0 + j);
-          const float4 w0 = *reinterpret_cast<const float4 *>(sW2 + c0 + j);
-          const float4 w1 = *reinterpret_cast<const float4 *>(sW2 + kN + c0 + j);
+          const float4 bb = *reinterpret_cast<const float4 *>(ep.b1 + c0 + j);
+          const float4 w0 = *reinterpret_cast<const float4 *>(ep.w2[0] + c0 + j);
+          const float4 w1 = *reinterpret_cast<const float4 *>(ep.w2[1] + c0 + j);
           float2 a01 = ffma2(make_float2(h[j], h[j + 1]), inv2, make_float2(bb.x, bb.y));
           float2 a23 = ffma2(make_float2(h[j + 2], h[j + 3]), inv2, make_float2(bb.z, bb.w));
           a01.x = fmaxf(a01.x, 0.f); a01.y = fmaxf(a01.y, 0.f);
@@ -542,7 +546,7 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
-  const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (3 * kN + 2 * kM) +
+  const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (2 * kM) +
                     sizeof(int) * 2 * kM + 8 * 6 + sizeof(int2) * kProdWarps * 2 * kRowsPerWarp +
                     16 + 1024;  // + SW128 alignment slack
   auto kern = k_predict_tc<DV, HALF>;
@@ -561,8 +565,14 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   const int64_t min_local = tiles / grid;
   const bool zero = zero_buf && zero_units > 0 &&
                     (zero_units + grid - 1) / grid <= min_local * kZeroPerTile;
+  EpiParams ep;
+  std::copy(mlp.hb1, mlp.hb1 + kN, ep.b1);
+  std::copy(mlp.hW2, mlp.hW2 + kN, ep.w2[0]);
+  std::copy(mlp.hW2 + kN, mlp.hW2 + 2 * kN, ep.w2[1]);
+  ep.b2[0] = mlp.hb2[0];
+  ep.b2[1] = mlp.hb2[1];
   kern<<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
-                                  err, zero ? zero_buf : nullptr, zero ? zero_units : 0);
+                                  err, zero ? zero_buf : nullptr, zero ? zero_units : 0, ep);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   if (zeroed) *zeroed = zero;
   return 1;

@@ -445,6 +445,9 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   }
   const int IN = 2 * D;
   c->hW1.assign(cfg->h_W1, cfg->h_W1 + (size_t)c->hidden * IN);
+  c->hb1.assign(cfg->h_b1, cfg->h_b1 + c->hidden);
+  c->hW2.assign(cfg->h_W2, cfg->h_W2 + 2 * (size_t)c->hidden);
+  c->hb2.assign(cfg->h_b2, cfg->h_b2 + 2);
   std::vector<float> hW1t((size_t)IN * c->hidden);
   for (int h = 0; h < c->hidden; ++h)
     for (int k = 0; k < IN; ++k) hW1t[(size_t)k * c->hidden + h] = c->hW1[(size_t)h * IN + k];

@@ -47,6 +47,8 @@ struct MLP {
   int hidden;
   int half_kind;         // 0: BF16, 1: FP16 (for W1h)
   int pooled_half;       // 1: the pooled grid is FP16 and already divided by the counts
+  // host copies of b1, W2, b2 (kernel parameters of the tensor-core head)
+  const float *hb1 = nullptr, *hW2 = nullptr, *hb2 = nullptr;
 };
 
 // Launch shapes picked by the autotuner (batch.cu); 0 keeps the built-in
