@@ -444,14 +444,14 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     }
   };
 
-  // HALF: reciprocal window counts of output block bb, one per lane
-  auto load_inv = [&](int bb) {
+  // HALF: window counts of output block bb, one per lane (the reciprocal is
+  // taken where they are used, a block later, so the load is not waited on)
+  auto load_cnt = [&](int bb) {
     const int q = lane < L ? lane : 0;
     const int j = bb * L + q;
-    const int n = j < nout ? __ldg(ncnt + (size_t)(o0 + j) * g.W + line) : 0;
-    return n > 0 ? 1.0f / (float)n : 0.f;
+    return j < nout ? __ldg(ncnt + (size_t)(o0 + j) * g.W + line) : 0;
   };
-  float inv_next = HALF ? load_inv(0) : 0.f;
+  int cnt_next = HALF ? load_cnt(0) : 0;
 
   issue(0);
   issue(1);
@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     }
     float inv_lane = 0.f;  // HALF: 1/n of output j0 + lane (lanes < L), loaded a block ahead
     if (HALF) {
-      inv_lane = inv_next;
-      if (b + 1 < nb) inv_next = load_inv(b + 1);
+      inv_lane = cnt_next > 0 ? 1.0f / (float)cnt_next : 0.f;
+      if (b + 1 < nb) cnt_next = load_cnt(b + 1);
     }
     auto emit = [&](int j, int qs, const float4 *G) {
       const int pos = o0 + j;

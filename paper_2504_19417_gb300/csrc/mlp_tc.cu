@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
     };
     int c_outk = -1;
     float c_inv = 0.f;
+    int n_cnt = 0;  // FP32 grid: window count of this lane's row in the next tile
     // pixels of this lane's row in the tile two ahead of the current one,
     // whose pooled rows are prefetched into L2 (sorted path only)
     int pf_pix = -1;
@@ -401,11 +402,12 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
           if (lane < kRowsPerWarp) ms[(b ^ 1) * kRowsPerWarp + lane] = make_int2(n_pix, (int)n_trel);
           __syncwarp();
           issue(b ^ 1, 0, qa);
-          // FP32 grid: 1/n of the next tile's rows, consumed at that tile's end
-          if (!HALF && n_inv != 0.f) n_inv = 1.0f / (float)__ldg(ncnt + n_pix);
         }
         if (h & 1) compute(b, h * kB, qb, Abuf);
         else compute(b, h * kB, qa, Abuf);
+        // FP32 grid: the window count of the next tile's row, loaded mid-tile
+        // (its pixel has arrived by then) and inverted at the tile's end
+        if (!HALF && h == NB / 2 - 1 && has_next && n_inv != 0.f) n_cnt = __ldg(ncnt + n_pix);
       }
       // the epilogue reads these after the full barrier
       if (lane < kRowsPerWarp) {
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(full_bar(b));
       c_outk = n_outk;
-      c_inv = n_inv;
+      c_inv = (!HALF && n_inv != 0.f) ? 1.0f / (float)n_cnt : n_inv;
     }
   } else {
     // ------------------------------------------------------------ epilogue
