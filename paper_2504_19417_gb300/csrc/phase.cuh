@@ -8,7 +8,9 @@
 // are below 2^-32 turn.  The angle handed to the sine/cosine therefore always
 // lies in [-pi, pi): no large-argument trigonometry ever happens, whatever the
 // slice length.  Error budget per component: 2^-24 turn quantisation
-// (3.7e-7 rad) plus __sincosf on [-pi, pi] (about 3.6e-7 absolute).
+// (3.7e-7 rad), the one rounding of x 2pi - 3pi below together with the FP32
+// constants (at most 4e-7 rad), and __sincosf on [-pi, pi] (about 3.6e-7
+// absolute).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,11 +22,12 @@ __device__ __forceinline__ float2 turn_phase(uint32_t t, uint32_t wlo, uint32_t 
   // top 32 bits of t * w64 + 1/2 turn (mod 2^64), plus half a unit of the
   // 23-bit fraction kept below: fr / 2^32 = frac(t w + 1/2)
   const uint32_t fr = __umulhi(t, wlo) + t * whi + 0x80000100u;
-  // 1.f with that fraction as mantissa, minus 1.5: frac(t w + 1/2) - 1/2, which
-  // lies in [-1/2, 1/2) and equals t w modulo whole turns
-  const float f = __uint_as_float(0x3f800000u | (fr >> 9)) - 1.5f;
+  // x = 1.f with that fraction as mantissa; (x - 3/2) turns = frac(t w + 1/2)
+  // - 1/2 lies in [-1/2, 1/2) and equals t w modulo whole turns; the angle
+  // (x - 3/2) 2 pi is formed in one fused multiply-add
+  const float x = __uint_as_float(0x3f800000u | (fr >> 9));
   float s, c;
-  __sincosf(f * 6.28318530717958647692f, &s, &c);
+  __sincosf(fmaf(x, 6.28318530717958647692f, -9.42477796076937971538f), &s, &c);
   return make_float2(c, s);
 }
 
