@@ -318,9 +318,10 @@ veckm_status veckm_autotune(veckm_ctx *ctx, int32_t width, int32_t height, void 
  * Algorithm 1).  A stream keeps its window's per-pixel phase sums and counts
  * resident on the device and updates them per pushed packet: the packet's
  * events are added and the events that left the window subtracted.  The sums
- * are held in 64-bit fixed point, into which every FP32 phase converts
- * exactly, so the resident sums stay bit-identical to sums built from the
- * window's events alone, however many packets pass (no drift, no rebuild).
+ * are held in 64-bit fixed point (units of 2^-32; each event adds and later
+ * subtracts the same integers), so the resident sums stay bit-identical to
+ * sums built from the window's events alone, however many packets pass (no
+ * drift, no rebuild).
  * The context supplies the sensor, D, the window radii, dt, the weights and
  * its scratch buffers; calls on a stream and on its context are ordered on
  * one CUDA stream. */

@@ -5,12 +5,13 @@
 // events, so a window that slides is kept up to date by adding the events of
 // each new packet and subtracting the events that leave the window.  To keep
 // that exact over any number of packets the per-pixel sums are held in 64-bit
-// fixed point: every component of an event's FP32 phase exp(i t T_d/dt) is an
-// integer multiple of 2^-32 (at most 24 significant bits, magnitude at most
-// one), so v * 2^32 converts to int64 without rounding, and integer addition
-// is exact and independent of order.  After any sequence of packets the
-// accumulator equals, bit for bit, the one built from the window's events
-// alone.  Counts are exact int32.
+// fixed point: each component v of an event's FP32 phase exp(i t T_d/dt)
+// becomes the integer v * 2^32 (exact for |v| >= 2^-8, where the FP32 spacing
+// is at least 2^-32; smaller components lose their bits below 2^-32, under
+// 2.4e-10), and integer addition is exact and independent of order.  An event
+// adds and later subtracts the same integers, so after any sequence of
+// packets the accumulator equals, bit for bit, the one built from the
+// window's events alone.  Counts are exact int32.
 //
 // The stream's valid events live in a device ring (x, y, t; t in absolute
 // microseconds), in time order as long as packets arrive in time order and
@@ -26,8 +27,9 @@
 //   4. append the valid events that fit (K[i] = an event's ring slot, or -1:
 //      its output row is zeroed and the error word set);
 //   5. add them;
-//   6. convert the accumulator to the FP32 grid and run the pooling and the
-//      gather (and perceptron) for the packet's events.
+//   6. convert the pixels whose sums changed to the stream's FP32 grid and
+//      run the pooling and the gather (and perceptron) for the packet's
+//      events.
 // Nothing is copied to the host: a push never synchronises.
 #include <cuda_runtime.h>
 
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256)
                  const int16_t *__restrict__ rx, const int16_t *__restrict__ ry,
                  const uint32_t *__restrict__ rt, long long cap, int W, int U,
                  const uint2 *__restrict__ wt, long long *__restrict__ acc64,
-                 int *__restrict__ cnt) {
+                 int *__restrict__ cnt, uint8_t *__restrict__ dirty) {
   const int lane = threadIdx.x & 31;
   const long long first = sign < 0 ? st->tail_old : st->head_old;
   const long long count = sign < 0 ? st->tail - st->tail_old : st->app;
@@ -123,7 +125,10 @@ __global__ void __launch_bounds__(256)
       red_add_s64(dst + 4 * u + 2, (long long)(ph.z * sc));
       red_add_s64(dst + 4 * u + 3, (long long)(ph.w * sc));
     }
-    if (lane == 0) atomicAdd(cnt + p, sign);
+    if (lane == 0) {
+      atomicAdd(cnt + p, sign);
+      dirty[p] = 1;
+    }
   }
 }
 
@@ -158,16 +163,37 @@ __global__ void k_ring_advance(RingState *st) {
   if (threadIdx.x == 0) st->head = st->head_old + st->app;
 }
 
-// 6. the window's accumulator as the FP32 grid of the pooling passes
-__global__ void k_fixed_to_float(const long long *__restrict__ acc64, float4 *__restrict__ acc,
-                                 long long units) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= units) return;
-  const longlong2 a = reinterpret_cast<const longlong2 *>(acc64)[2 * i];
-  const longlong2 b = reinterpret_cast<const longlong2 *>(acc64)[2 * i + 1];
+// 6. the stream's FP32 grid for the pixels whose sums changed since the last
+// push (marked by k_ring_apply): a warp takes 32 pixels, ballots their marks
+// and converts each marked pixel with all lanes (rounding each 64-bit sum to
+// the nearest FP32), then clears the marks.  An unchanged sum converts to the
+// same FP32 value, so unmarked pixels keep their previous conversion.
+__global__ void __launch_bounds__(256) k_fixed_to_float_dirty(const long long *__restrict__ acc64,
+                                                              float4 *__restrict__ acc,
+                                                              uint8_t *__restrict__ dirty,
+                                                              long long P, int U) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   const float s = 2.3283064365386963e-10f;  // 2^-32
-  acc[i] = make_float4(__ll2float_rn(a.x) * s, __ll2float_rn(a.y) * s, __ll2float_rn(b.x) * s,
-                       __ll2float_rn(b.y) * s);
+  for (long long p0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+       p0 < P; p0 += nw * 32) {
+    const long long pl = p0 + lane;
+    const bool mark = pl < P && dirty[pl] != 0;
+    unsigned m = __ballot_sync(0xffffffffu, mark);
+    if (mark) dirty[pl] = 0;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const long long p = p0 + b;
+      for (int u = lane; u < U; u += 32) {
+        const size_t i = (size_t)p * U + u;
+        const longlong2 a = reinterpret_cast<const longlong2 *>(acc64)[2 * i];
+        const longlong2 c = reinterpret_cast<const longlong2 *>(acc64)[2 * i + 1];
+        acc[i] = make_float4(__ll2float_rn(a.x) * s, __ll2float_rn(a.y) * s,
+                             __ll2float_rn(c.x) * s, __ll2float_rn(c.y) * s);
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -179,6 +205,8 @@ struct veckm_stream {
   veckm_ctx *c = nullptr;
   int64_t window = 0, cap = 0;
   long long *acc64 = nullptr;
+  float4 *accf = nullptr;    // the window's per-pixel sums in FP32 (the row pass input)
+  uint8_t *dirty = nullptr;  // pixels whose sums changed since the last conversion
   int *cnt = nullptr;
   int16_t *rx = nullptr, *ry = nullptr;
   uint32_t *rt = nullptr;
@@ -203,6 +231,8 @@ veckm_status veckm_stream_create(veckm_ctx *c, int64_t window_us, int64_t capaci
   s->cap = capacity;
   const size_t P = (size_t)c->g.W * c->g.H;
   cudaError_t e = cudaMalloc(&s->acc64, P * (size_t)c->g.U * 4 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&s->accf, P * (size_t)c->g.U * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&s->dirty, P);
   if (e == cudaSuccess) e = cudaMalloc(&s->cnt, P * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&s->rx, (size_t)capacity * 2);
   if (e == cudaSuccess) e = cudaMalloc(&s->ry, (size_t)capacity * 2);
@@ -215,6 +245,8 @@ veckm_status veckm_stream_create(veckm_ctx *c, int64_t window_us, int64_t capaci
   if (e == cudaSuccess) e = cudaMalloc(&s->bsum, (size_t)scan_blocks(capacity) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->nvalid, 4);
   if (e == cudaSuccess) e = cudaMemset(s->acc64, 0, P * (size_t)c->g.U * 4 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(s->accf, 0, P * (size_t)c->g.U * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMemset(s->dirty, 0, P);
   if (e == cudaSuccess) e = cudaMemset(s->cnt, 0, P * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s->st, 0, sizeof(RingState));
   if (e != cudaSuccess) {
@@ -236,16 +268,16 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   if (predict && g.D > 128 && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)))
     return fail_msg(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
   cudaStream_t cs = (cudaStream_t)stream;
-  grids_dirty(c);  // the push converts its sums into acc and pools through hbuf
+  grids_dirty(c);  // the push pools through hbuf into acc
   const uint32_t t_lo = t_hi_us >= (uint64_t)s->window ? t_hi_us - (uint32_t)s->window : 0u;
   const int DV = g.U / 32;
   auto apply = [&](int sign) {
     const int blocks = num_sms() * 8;
     switch (DV) {
-      case 1: k_ring_apply<1><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
-      case 2: k_ring_apply<2><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
-      case 3: k_ring_apply<3><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
-      default: k_ring_apply<4><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt); break;
+      case 1: k_ring_apply<1><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
+      case 2: k_ring_apply<2><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
+      case 3: k_ring_apply<3><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
+      default: k_ring_apply<4><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
     }
   };
   int launches = 0;
@@ -281,13 +313,14 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
     return VECKM_OK;
   }
   // 6. the window's grid, pooling, then the packet's outputs
-  const long long units = (long long)g.W * g.H * g.U;
-  k_fixed_to_float<<<(unsigned)((units + 255) / 256), 256, 0, cs>>>(s->acc64, c->acc, units);
+  const long long P = (long long)g.W * g.H;
+  k_fixed_to_float_dirty<<<(unsigned)std::min<long long>((P + 255) / 256, (long long)num_sms() * 8),
+                           256, 0, cs>>>(s->acc64, s->accf, s->dirty, P, g.U);
   launches += 1;
   const Tables tb = c->tables();
   const Tune tn = c->tune_for(g);
   int r;
-  if ((r = launch_pool_rows(g, tb, c->acc, c->hbuf, cs, tn)) < 0) return fail_cuda(cudaGetLastError(), "pooling (rows) launch");
+  if ((r = launch_pool_rows(g, tb, s->accf, c->hbuf, cs, tn)) < 0) return fail_cuda(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   if ((r = launch_counts(g, s->cnt, c->cnt_tmp, c->ncnt, cs)) < 0) return fail_cuda(cudaGetLastError(), "window count launch");
   launches += r;
@@ -337,7 +370,7 @@ veckm_status veckm_stream_accumulator(veckm_stream *s, int64_t *h_acc, int32_t *
 void veckm_stream_destroy(veckm_stream *s) {
   if (!s) return;
   cudaDeviceSynchronize();
-  void *ptrs[] = {s->acc64, s->cnt, s->rx, s->ry, s->rt, s->K, s->st,
+  void *ptrs[] = {s->acc64, s->accf, s->dirty, s->cnt, s->rx, s->ry, s->rt, s->K, s->st,
                   s->flag, s->off, s->cur, s->bsum, s->nvalid};
   for (void *p : ptrs)
     if (p) cudaFree(p);
