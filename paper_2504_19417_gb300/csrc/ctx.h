@@ -45,9 +45,12 @@ struct veckm_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
   int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
-  // pixel-sorted event records (grown on demand)
+  // pixel-sorted event records (grown on demand), and the bucket sort's
+  // records grouped by bucket, per-tile bucket counts and bucket totals
   int2 *rec = nullptr;
   int *rpix = nullptr;
+  int4 *brec = nullptr;
+  int *bhist = nullptr, *btot = nullptr;
   int64_t rec_cap = 0;
   std::vector<float> hW1;  // host copy (re-encoding on precision switch)
   std::vector<float> hb1, hW2, hb2;  // host copies (kernel parameters)

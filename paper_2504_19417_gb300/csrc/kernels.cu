@@ -255,6 +255,273 @@ __global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__res
   }
 }
 
+// 1-3 (bucket form).  The same outputs as k_hist + scan + k_place (records
+// grouped by pixel, per-pixel counts, the record total) without global
+// atomics, and with coalesced writes.  Pixels are grouped into nb buckets of
+// 2^shift consecutive pixels; events into tiles of consecutive indices.
+//   a. k_bucket_count: per tile, events per bucket (shared-memory atomics);
+//      also validates the events (error word, zeroed flows) as k_hist does.
+//   b. k_bucket_scan: per bucket, exclusive prefix of its counts over tiles,
+//      and the bucket's total.
+//   c. k_bucket_scatter: per tile, the valid events (t - t_ref, index, pixel)
+//      ranked by bucket in shared memory, then written bucket run by bucket
+//      run to the buckets' regions at the tile's cursors.
+//   d. k_bucket_sort: per bucket, a counting sort of its records by pixel in
+//      shared memory, written out in order (buckets above kSortStage records
+//      place them straight into the bucket's region instead); also writes
+//      the pixel counts.
+// Records of one pixel come out in no particular order, as with k_place.
+constexpr int kSortThreads = 512;
+constexpr int kMaxBuckets = 1024;
+constexpr int kMaxBucketShift = 15;  // 32768 pixels: a 128 KB shared histogram
+constexpr int kMaxSortTiles = 4096;
+constexpr int kSortILP = 8;        // events or records in flight per thread
+constexpr int kSortStage = 4096;   // records a bucket sorts in shared memory
+
+// Exclusive prefix of v[0..nb) into out[0..nb) (out may be v) and the sum in
+// *total, for nb <= 2 * blockDim.x (one block; s_warp holds 33 ints).
+__device__ void block_scan_small(const int *v, int nb, int *out, int *total, int *s_warp) {
+  const int i0 = 2 * threadIdx.x;
+  const int a = i0 < nb ? v[i0] : 0, b = i0 + 1 < nb ? v[i0 + 1] : 0;
+  int tot;
+  const int ex = block_excl_scan(a + b, s_warp, tot);
+  if (i0 < nb) out[i0] = ex;
+  if (i0 + 1 < nb) out[i0 + 1] = ex + a;
+  if (total && threadIdx.x == 0) *total = tot;
+}
+
+// The events of tile blockIdx.x: x, y, t from offset k0, m of them.
+struct TileEvents {
+  const int16_t *x, *y;
+  const uint32_t *t;
+  int64_t k0;
+  int m;
+  __device__ TileEvents(const Events &ev, int per_tile) {
+    k0 = (int64_t)blockIdx.x * per_tile;
+    m = (int)(k0 + per_tile < ev.n ? per_tile : ev.n - k0);
+    x = ev.x + k0;
+    y = ev.y + k0;
+    t = ev.t + k0;
+  }
+};
+
+// bhist is tile-major: bhist[tile * nb + bucket]
+__global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geometry g, int shift,
+                                                                  int nb, int per_tile,
+                                                                  int *__restrict__ bhist,
+                                                                  int *__restrict__ err,
+                                                                  float *__restrict__ zero_flow) {
+  __shared__ int h[kMaxBuckets];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const TileEvents te(ev, per_tile);
+  // kSortILP events per thread and round: every load first, then the atomics
+  for (int jb = threadIdx.x; jb < te.m; jb += kSortILP * blockDim.x) {
+    int x[kSortILP], y[kSortILP];
+    uint32_t t[kSortILP];
+#pragma unroll
+    for (int e = 0; e < kSortILP; ++e) {
+      const int j = jb + e * blockDim.x;
+      x[e] = j < te.m ? te.x[j] : -1;
+      y[e] = j < te.m ? te.y[j] : 0;
+      t[e] = j < te.m ? te.t[j] : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < kSortILP; ++e) {
+      const int j = jb + e * blockDim.x;
+      if (j >= te.m) continue;
+      uint32_t trel;
+      if (event_ok(x[e], y[e], t[e], ev, g.W, g.H, trel)) {
+        atomicAdd(&h[(y[e] * g.W + x[e]) >> shift], 1);
+      } else {
+        atomicOr(err, ERR_EVENT_RANGE);
+        if (zero_flow)
+          *reinterpret_cast<float2 *>(zero_flow + 2 * (te.k0 + j)) = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) bhist[(size_t)blockIdx.x * nb + i] = h[i];
+}
+
+// one block per bucket (4 tiles per thread): its column of tile counts
+// becomes exclusive prefixes, and btot[bucket] the bucket's total
+__global__ void __launch_bounds__(1024) k_bucket_scan(int *__restrict__ bhist, int nb, int tiles,
+                                                      int *__restrict__ btot) {
+  __shared__ int s_warp[33];
+  const int b = blockIdx.x;
+  const int i0 = 4 * threadIdx.x;
+  int c[4], v = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    c[q] = i0 + q < tiles ? bhist[(size_t)(i0 + q) * nb + b] : 0;
+    v += c[q];
+  }
+  int tot;
+  int run = block_excl_scan(v, s_warp, tot);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (i0 + q < tiles) bhist[(size_t)(i0 + q) * nb + b] = run;
+    run += c[q];
+  }
+  if (threadIdx.x == 0) btot[b] = tot;
+}
+
+// dynamic shared memory: per_tile int4 records and per_tile ints
+__global__ void __launch_bounds__(kSortThreads) k_bucket_scatter(Events ev, Geometry g, int shift,
+                                                                 int nb, int per_tile,
+                                                                 const int *__restrict__ bhist,
+                                                                 const int *__restrict__ btot,
+                                                                 int4 *__restrict__ brec) {
+  extern __shared__ int4 stage[];                             // (t - t_ref, index, pixel, rank)
+  int *src = reinterpret_cast<int *>(stage + per_tile);       // tile slot of the d-th record
+  __shared__ int cur[kMaxBuckets];  // global position of this tile's first record per bucket
+  __shared__ int loc[kMaxBuckets];  // records per bucket in the tile, then their offsets
+  __shared__ int s_warp[33];
+  block_scan_small(btot, nb, cur, nullptr, s_warp);  // bucket bases
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) loc[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] += bhist[(size_t)blockIdx.x * nb + i];
+  const TileEvents te(ev, per_tile);
+  // rank every valid event within its bucket (shared atomics)
+  for (int jb = threadIdx.x; jb < te.m; jb += kSortILP * blockDim.x) {
+    int x[kSortILP], y[kSortILP];
+    uint32_t t[kSortILP];
+#pragma unroll
+    for (int e = 0; e < kSortILP; ++e) {
+      const int j = jb + e * blockDim.x;
+      x[e] = j < te.m ? te.x[j] : -1;
+      y[e] = j < te.m ? te.y[j] : 0;
+      t[e] = j < te.m ? te.t[j] : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < kSortILP; ++e) {
+      const int j = jb + e * blockDim.x;
+      if (j >= te.m) continue;
+      uint32_t trel;
+      if (event_ok(x[e], y[e], t[e], ev, g.W, g.H, trel)) {
+        const int p = y[e] * g.W + x[e];
+        stage[j] = make_int4((int)trel, (int)(te.k0 + j), p, atomicAdd(&loc[p >> shift], 1));
+      } else {
+        stage[j] = make_int4(0, 0, -1, 0);
+      }
+    }
+  }
+  __syncthreads();
+  int nvalid;
+  block_scan_small(loc, nb, loc, &nvalid, s_warp);
+  if (threadIdx.x == 0) s_warp[32] = nvalid;  // block_excl_scan's slot, free again here
+  __syncthreads();
+  nvalid = s_warp[32];
+  for (int j = threadIdx.x; j < te.m; j += blockDim.x) {
+    const int4 r = stage[j];
+    if (r.z >= 0) src[loc[r.z >> shift] + r.w] = j;
+  }
+  __syncthreads();
+  // the tile's records in bucket order: each bucket's run lands contiguously
+  for (int d = threadIdx.x; d < nvalid; d += blockDim.x) {
+    const int4 r = stage[src[d]];
+    const int b = r.z >> shift;
+    brec[cur[b] + (d - loc[b])] = r;
+  }
+}
+
+// one block per bucket (dynamic shared memory: 2^shift ints for the pixel
+// histogram, then kSortStage int4 records and kSortStage ints)
+__global__ void __launch_bounds__(kSortThreads) k_bucket_sort(const int4 *__restrict__ brec,
+                                                              int shift, int nb, int64_t P,
+                                                              const int *__restrict__ btot,
+                                                              int *__restrict__ cnt,
+                                                              int *__restrict__ total_out,
+                                                              int2 *__restrict__ rec,
+                                                              int *__restrict__ rpix) {
+  extern __shared__ int hs[];
+  const int width = 1 << shift;
+  int4 *stage = reinterpret_cast<int4 *>(hs + ((width + 3) & ~3));
+  int *src = reinterpret_cast<int *>(stage + kSortStage);
+  __shared__ int s_warp[33];
+  __shared__ int s_base[2];
+  const int b = blockIdx.x;
+  const int64_t p0 = (int64_t)b << shift;
+  // this bucket's first record: the sum of the earlier buckets' totals
+  {
+    int v = 0;
+    for (int i = threadIdx.x; i < b; i += blockDim.x) v += btot[i];
+    int tot;
+    block_excl_scan(v, s_warp, tot);
+    if (threadIdx.x == 0) {
+      s_base[0] = tot;
+      s_base[1] = btot[b];
+    }
+  }
+  for (int i = threadIdx.x; i < width; i += blockDim.x) hs[i] = 0;
+  __syncthreads();
+  const int base = s_base[0], nrec = s_base[1];
+  const bool staged = nrec <= kSortStage;
+  // histogram (and, staged, each record with its rank among its pixel's)
+  for (int rb = threadIdx.x; rb < nrec; rb += kSortILP * blockDim.x) {
+    int4 q[kSortILP];
+#pragma unroll
+    for (int e = 0; e < kSortILP; ++e) {
+      const int r = rb + e * blockDim.x;
+      q[e] = r < nrec ? brec[base + r] : make_int4(0, 0, -1, 0);
+    }
+#pragma unroll
+    for (int e = 0; e < kSortILP; ++e) {
+      if (q[e].z < 0) continue;
+      const int rank = atomicAdd(&hs[q[e].z - p0], 1);
+      if (staged) stage[rb + e * blockDim.x] = make_int4(q[e].x, q[e].y, q[e].z, rank);
+    }
+  }
+  __syncthreads();
+  // counts out; hs becomes each pixel's first slot in the bucket (exclusive prefix)
+  const int per = (width + blockDim.x - 1) / blockDim.x;
+  const int i0 = threadIdx.x * per;
+  int v = 0;
+  for (int q = 0; q < per && i0 + q < width; ++q) {
+    const int c = hs[i0 + q];
+    if (p0 + i0 + q < P) cnt[p0 + i0 + q] = c;
+    v += c;
+  }
+  int tot;
+  int run = block_excl_scan(v, s_warp, tot);
+  for (int q = 0; q < per && i0 + q < width; ++q) {
+    const int c = hs[i0 + q];
+    hs[i0 + q] = run;
+    run += c;
+  }
+  __syncthreads();
+  if (staged) {
+    for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+      const int4 q = stage[r];
+      src[hs[q.z - p0] + q.w] = r;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nrec; d += blockDim.x) {  // in order: coalesced
+      const int4 q = stage[src[d]];
+      rec[base + d] = make_int2(q.x, q.y);
+      rpix[base + d] = q.z;
+    }
+  } else {
+    for (int rb = threadIdx.x; rb < nrec; rb += kSortILP * blockDim.x) {
+      int4 q[kSortILP];
+#pragma unroll
+      for (int e = 0; e < kSortILP; ++e) {
+        const int r = rb + e * blockDim.x;
+        q[e] = r < nrec ? brec[base + r] : make_int4(0, 0, -1, 0);
+      }
+#pragma unroll
+      for (int e = 0; e < kSortILP; ++e) {
+        if (q[e].z < 0) continue;
+        const int pos = base + atomicAdd(&hs[q[e].z - p0], 1);
+        rec[pos] = make_int2(q[e].x, q[e].y);
+        rpix[pos] = q[e].z;
+      }
+    }
+  }
+  if (b == nb - 1 && threadIdx.x == 0) *total_out = base + nrec;
+}
+
 // 4. per-pixel phase sums PixelEmbed[p] = sum over the pixel's records of
 // exp(i t T/dt), into an accumulator cleared beforehand (empty pixels stay
 // zero).  Work is balanced by records: warp c takes records
@@ -1131,6 +1398,60 @@ int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *
                                           (int64_t)num_sms() * 8);
   k_place<<<grid, 256, 0, s>>>(ev, g, cur, rec, pix);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int bucket_sort_shift(int64_t P) {
+  int shift = 0;
+  while (((P + (1LL << shift) - 1) >> shift) > kMaxBuckets) ++shift;
+  return shift <= kMaxBucketShift ? shift : -1;
+}
+
+int bucket_sort_max_buckets() { return kMaxBuckets; }
+
+int bucket_sort_max_tiles() { return kMaxSortTiles; }
+
+// events per tile: one round of the block, or two for inputs that would
+// need more than kMaxSortTiles tiles; 0 when even that is too many
+static int64_t bucket_sort_tile(int64_t n) {
+  const int64_t one = (int64_t)kSortILP * kSortThreads;
+  if (n <= one * kMaxSortTiles) return one;
+  if (n <= 2 * one * kMaxSortTiles) return 2 * one;
+  return 0;
+}
+
+bool bucket_sort_fits(int64_t P, int64_t n) {
+  return bucket_sort_shift(P) >= 0 && bucket_sort_tile(n) > 0;
+}
+
+int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total, int2 *rec,
+                       int *rpix, int4 *brec, int *bhist, int *btot, int *err, float *zero_flow,
+                       cudaStream_t s) {
+  const int64_t P = (int64_t)g.W * g.H;
+  const int shift = bucket_sort_shift(P);
+  const int64_t per_tile = bucket_sort_tile(ev.n);
+  if (shift < 0 || per_tile == 0) return -1;
+  const int nb = (int)((P + (1LL << shift) - 1) >> shift);
+  if (ev.n == 0) {
+    if (cudaMemsetAsync(cnt, 0, (size_t)P * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(total, 0, sizeof(int), s) != cudaSuccess)
+      return -1;
+    return 0;
+  }
+  const int tiles = (int)((ev.n + per_tile - 1) / per_tile);
+  const size_t scatter_sm = (size_t)per_tile * (sizeof(int4) + sizeof(int));
+  const size_t sort_sm = ((((size_t)1 << shift) + 3) & ~(size_t)3) * sizeof(int) +
+                         (size_t)kSortStage * (sizeof(int4) + sizeof(int));
+  if (set_smem(k_bucket_scatter, scatter_sm) != cudaSuccess ||
+      set_smem(k_bucket_sort, sort_sm) != cudaSuccess)
+    return -1;
+  const int scan_threads = std::min(1024, ((tiles + 3) / 4 + 31) / 32 * 32);
+  k_bucket_count<<<tiles, kSortThreads, 0, s>>>(ev, g, shift, nb, (int)per_tile, bhist, err,
+                                               zero_flow);
+  k_bucket_scan<<<nb, scan_threads, 0, s>>>(bhist, nb, tiles, btot);
+  k_bucket_scatter<<<tiles, kSortThreads, scatter_sm, s>>>(ev, g, shift, nb, (int)per_tile, bhist,
+                                                          btot, brec);
+  k_bucket_sort<<<nb, kSortThreads, sort_sm, s>>>(brec, shift, nb, P, btot, cnt, total, rec, rpix);
+  return cudaPeekAtLastError() == cudaSuccess ? 4 : -1;
 }
 
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,

@@ -106,7 +106,8 @@ void free_all(veckm_ctx *c) {
   c->pipe = nullptr;
   void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
                   c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
-                  c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->cx, c->cy, c->ct,
+                  c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->brec, c->bhist, c->btot,
+                  c->cx, c->cy, c->ct,
                   c->slice_tab, c->wxy, c->rx, c->ry};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -165,11 +166,14 @@ veckm_status ensure_records(veckm_ctx *c, int64_t n, cudaStream_t s) {
   cudaError_t e = cudaStreamSynchronize(s);
   if (c->rec) cudaFree(c->rec);
   if (c->rpix) cudaFree(c->rpix);
+  if (c->brec) cudaFree(c->brec);
   c->rec = nullptr;
   c->rpix = nullptr;
+  c->brec = nullptr;
   c->rec_cap = 0;
   if (e == cudaSuccess) e = dalloc(&c->rec, (size_t)n);
   if (e == cudaSuccess) e = dalloc(&c->rpix, (size_t)n);
+  if (e == cudaSuccess) e = dalloc(&c->brec, (size_t)n);
   if (e != cudaSuccess) return cuda_fail(e, "event record buffers");
   c->rec_cap = n;
   return VECKM_OK;
@@ -210,14 +214,27 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
                                     (c->path == VECKM_PATH_AUTO && t_direct < t_dense));
   c->last_path = direct ? VECKM_PATH_DIRECT : VECKM_PATH_DENSE;
   mark();
-  cudaError_t e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
-  if (e != cudaSuccess) return cuda_fail(e, "clearing the counts");
-  if ((r = launch_hist(ev, g, c->cnt, c->err, (sorted && !direct) ? out : nullptr, s)) < 0)
-    return cuda_fail(cudaGetLastError(), "histogram launch");
-  launches += r;
-  if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s)) < 0)
-    return cuda_fail(cudaGetLastError(), "scan launch");
-  launches += r;
+  // Sort by pixel: the bucket form (no global atomics) where the geometry
+  // fits its limits, else histogram, scan and placement with global cursors.
+  // Both give the per-pixel counts, the record total (off[P]) and the
+  // pixel-grouped records.
+  float *zero_flow = (sorted && !direct) ? out : nullptr;
+  const bool bucketed = bucket_sort_fits((int64_t)P, n);
+  if (bucketed) {
+    if ((r = launch_bucket_sort(ev, g, c->cnt, c->off + P, c->rec, c->rpix, c->brec, c->bhist,
+                                c->btot, c->err, zero_flow, s)) < 0)
+      return cuda_fail(cudaGetLastError(), "bucket sort launch");
+    launches += r;
+  } else {
+    cudaError_t e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the counts");
+    if ((r = launch_hist(ev, g, c->cnt, c->err, zero_flow, s)) < 0)
+      return cuda_fail(cudaGetLastError(), "histogram launch");
+    launches += r;
+    if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s)) < 0)
+      return cuda_fail(cudaGetLastError(), "scan launch");
+    launches += r;
+  }
   // The window counts need only the histogram: on the dense path they run on
   // the side stream, under the placement, pixel sums and row pass, and join
   // before the column pass (on every return once forked).
@@ -241,9 +258,11 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     if (r < 0 || fe != cudaSuccess) return cuda_fail(cudaGetLastError(), "window count launch");
     launches += r;
   }
-  if ((r = launch_place(ev, g, c->cur, c->rec, c->rpix, s)) < 0)
-    return cuda_fail(cudaGetLastError(), "placement launch");
-  launches += r;
+  if (!bucketed) {
+    if ((r = launch_place(ev, g, c->cur, c->rec, c->rpix, s)) < 0)
+      return cuda_fail(cudaGetLastError(), "placement launch");
+    launches += r;
+  }
   mark();
   if (direct) {
     if (c->zero_grid == 0) c->zero_grid = -1;  // the owned sums write acc
@@ -485,6 +504,11 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(dalloc(&c->cur, P));
   VK_TRY(dalloc(&c->bsum, (size_t)scan_blocks((int64_t)P)));
   VK_TRY(dalloc(&c->total, 1));
+  {  // a call's geometry is at most the context's, so at most min(P, max) buckets
+    const size_t nbmax = std::min<size_t>(P, (size_t)bucket_sort_max_buckets());
+    VK_TRY(dalloc(&c->bhist, nbmax * bucket_sort_max_tiles()));
+    VK_TRY(dalloc(&c->btot, nbmax));
+  }
   VK_TRY(dalloc(&c->err, 1));
   VK_TRY(cudaMallocHost(reinterpret_cast<void **>(&c->h_err), sizeof(int)));
   VK_TRY(cudaMemcpy(c->tx, htx.data(), htx.size() * 4, cudaMemcpyHostToDevice));

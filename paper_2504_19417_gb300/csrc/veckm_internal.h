@@ -69,6 +69,21 @@ int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur
                 cudaStream_t s);
 int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
                  cudaStream_t s);
+// The same outputs as launch_hist + launch_scan + launch_place (counts per
+// pixel, the record total in *total, pixel-grouped records) by a two-level
+// bucket sort without global atomics.  bucket_sort_shift: log2 of the pixels
+// per bucket for P pixels, or -1 when P is beyond the form's limits
+// (launch_bucket_sort returns -1 outside bucket_sort_fits).  A geometry of P pixels has at most
+// min(P, bucket_sort_max_buckets()) buckets.  brec: n records; bhist: that
+// many buckets times bucket_sort_max_tiles() ints; btot: one per bucket.
+int bucket_sort_shift(int64_t P);
+int bucket_sort_max_buckets();
+int bucket_sort_max_tiles();
+// Whether P pixels and n events are within the bucket form's limits.
+bool bucket_sort_fits(int64_t P, int64_t n);
+int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total, int2 *rec,
+                       int *rpix, int4 *brec, int *bhist, int *btot, int *err, float *zero_flow,
+                       cudaStream_t s);
 // Clears acc (unless the caller knows it is zero: clear = false), then sums
 // the *nsorted pixel-sorted records (n bounds it).
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
