@@ -344,9 +344,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geo
   for (int i = threadIdx.x; i < nb; i += blockDim.x) bhist[(size_t)blockIdx.x * nb + i] = h[i];
 }
 
-// one block per bucket (4 tiles per thread): its column of tile counts
-// becomes exclusive prefixes, and btot[bucket] the bucket's total
-__global__ void __launch_bounds__(1024) k_bucket_scan(int *__restrict__ bhist, int nb, int tiles,
+// one block per bucket (4 tiles per thread): the exclusive prefixes of its
+// column of tile counts go to bpre, the bucket's total to btot
+__global__ void __launch_bounds__(1024) k_bucket_scan(const int *__restrict__ bhist, int nb,
+                                                      int tiles, int *__restrict__ bpre,
                                                       int *__restrict__ btot) {
   __shared__ int s_warp[33];
   const int b = blockIdx.x;
@@ -361,74 +362,80 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(int *__restrict__ bhist, i
   int run = block_excl_scan(v, s_warp, tot);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (i0 + q < tiles) bhist[(size_t)(i0 + q) * nb + b] = run;
+    if (i0 + q < tiles) bpre[(size_t)(i0 + q) * nb + b] = run;
     run += c[q];
   }
   if (threadIdx.x == 0) btot[b] = tot;
 }
 
-// dynamic shared memory: per_tile int4 records and per_tile ints
-__global__ void __launch_bounds__(kSortThreads) k_bucket_scatter(Events ev, Geometry g, int shift,
-                                                                 int nb, int per_tile,
-                                                                 const int *__restrict__ bhist,
-                                                                 const int *__restrict__ btot,
-                                                                 int4 *__restrict__ brec) {
-  extern __shared__ int4 stage[];                             // (t - t_ref, index, pixel, rank)
-  int *src = reinterpret_cast<int *>(stage + per_tile);       // tile slot of the d-th record
+// dynamic shared memory: per_tile records as three int arrays (t - t_ref,
+// index, pixel) in bucket order
+__global__ void __launch_bounds__(kSortThreads, 3) k_bucket_scatter(Events ev, Geometry g, int shift,
+                                                                    int nb, int per_tile,
+                                                                    const int *__restrict__ bhist,
+                                                                    const int *__restrict__ bpre,
+                                                                    const int *__restrict__ btot,
+                                                                    int4 *__restrict__ brec) {
+  extern __shared__ int sst[];
+  int *st_t = sst, *st_k = sst + per_tile, *st_p = sst + 2 * per_tile;
   __shared__ int cur[kMaxBuckets];  // global position of this tile's first record per bucket
-  __shared__ int loc[kMaxBuckets];  // records per bucket in the tile, then their offsets
+  __shared__ int loc[kMaxBuckets];  // offset of each bucket's run within the tile
+  __shared__ int fil[kMaxBuckets];  // fill cursor of each run
   __shared__ int s_warp[33];
+  const int *cnt_tile = bhist + (size_t)blockIdx.x * nb;
   block_scan_small(btot, nb, cur, nullptr, s_warp);  // bucket bases
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) loc[i] = 0;
+  int nvalid;
+  block_scan_small(cnt_tile, nb, loc, &nvalid, s_warp);
+  if (threadIdx.x == 0) s_warp[32] = nvalid;  // block_excl_scan's slot, free again here
   __syncthreads();
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] += bhist[(size_t)blockIdx.x * nb + i];
+  nvalid = s_warp[32];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    cur[i] += bpre[(size_t)blockIdx.x * nb + i];
+    fil[i] = loc[i];
+  }
+  __syncthreads();
   const TileEvents te(ev, per_tile);
-  // rank every valid event within its bucket (shared atomics)
-  for (int jb = threadIdx.x; jb < te.m; jb += kSortILP * blockDim.x) {
-    int x[kSortILP], y[kSortILP];
-    uint32_t t[kSortILP];
+  // each valid event straight to its slot in its bucket's run (shared atomics)
+  constexpr int kILP = kSortILP / 2;
+  for (int jb = threadIdx.x; jb < te.m; jb += kILP * blockDim.x) {
+    int x[kILP], y[kILP];
+    uint32_t t[kILP];
 #pragma unroll
-    for (int e = 0; e < kSortILP; ++e) {
+    for (int e = 0; e < kILP; ++e) {
       const int j = jb + e * blockDim.x;
       x[e] = j < te.m ? te.x[j] : -1;
       y[e] = j < te.m ? te.y[j] : 0;
       t[e] = j < te.m ? te.t[j] : 0u;
     }
 #pragma unroll
-    for (int e = 0; e < kSortILP; ++e) {
+    for (int e = 0; e < kILP; ++e) {
       const int j = jb + e * blockDim.x;
-      if (j >= te.m) continue;
       uint32_t trel;
-      if (event_ok(x[e], y[e], t[e], ev, g.W, g.H, trel)) {
+      if (j < te.m && event_ok(x[e], y[e], t[e], ev, g.W, g.H, trel)) {
         const int p = y[e] * g.W + x[e];
-        stage[j] = make_int4((int)trel, (int)(te.k0 + j), p, atomicAdd(&loc[p >> shift], 1));
-      } else {
-        stage[j] = make_int4(0, 0, -1, 0);
+        const int d = atomicAdd(&fil[p >> shift], 1);
+        if (d < per_tile) {  // always, when the counts came from the same events
+          st_t[d] = (int)trel;
+          st_k[d] = (int)(te.k0 + j);
+          st_p[d] = p;
+        }
       }
     }
   }
   __syncthreads();
-  int nvalid;
-  block_scan_small(loc, nb, loc, &nvalid, s_warp);
-  if (threadIdx.x == 0) s_warp[32] = nvalid;  // block_excl_scan's slot, free again here
-  __syncthreads();
-  nvalid = s_warp[32];
-  for (int j = threadIdx.x; j < te.m; j += blockDim.x) {
-    const int4 r = stage[j];
-    if (r.z >= 0) src[loc[r.z >> shift] + r.w] = j;
-  }
-  __syncthreads();
   // the tile's records in bucket order: each bucket's run lands contiguously
+  nvalid = nvalid < te.m ? nvalid : te.m;
   for (int d = threadIdx.x; d < nvalid; d += blockDim.x) {
-    const int4 r = stage[src[d]];
-    const int b = r.z >> shift;
-    brec[cur[b] + (d - loc[b])] = r;
+    const int p = st_p[d];
+    const int b = p >> shift;
+    if (p < 0 || b >= nb) continue;
+    brec[cur[b] + (d - loc[b])] = make_int4(st_t[d], st_k[d], p, 0);
   }
 }
 
 // one block per bucket (dynamic shared memory: 2^shift ints for the pixel
-// histogram, then kSortStage int4 records and kSortStage ints)
-__global__ void __launch_bounds__(kSortThreads) k_bucket_sort(const int4 *__restrict__ brec,
+// histogram, then four arrays of kSortStage ints)
+__global__ void __launch_bounds__(kSortThreads, 3) k_bucket_sort(const int4 *__restrict__ brec,
                                                               int shift, int nb, int64_t P,
                                                               const int *__restrict__ btot,
                                                               int *__restrict__ cnt,
@@ -437,8 +444,10 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(const int4 *__rest
                                                               int *__restrict__ rpix) {
   extern __shared__ int hs[];
   const int width = 1 << shift;
-  int4 *stage = reinterpret_cast<int4 *>(hs + ((width + 3) & ~3));
-  int *src = reinterpret_cast<int *>(stage + kSortStage);
+  // staged records as three int arrays (t - t_ref, index, pixel) and each
+  // record's rank among its pixel's, then the source of each output slot
+  int *st_t = hs + width, *st_k = st_t + kSortStage, *st_p = st_k + kSortStage;
+  int *st_r = st_p + kSortStage, *src = st_r;  // ranks, then (reused) sources
   __shared__ int s_warp[33];
   __shared__ int s_base[2];
   const int b = blockIdx.x;
@@ -459,18 +468,27 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(const int4 *__rest
   const int base = s_base[0], nrec = s_base[1];
   const bool staged = nrec <= kSortStage;
   // histogram (and, staged, each record with its rank among its pixel's)
-  for (int rb = threadIdx.x; rb < nrec; rb += kSortILP * blockDim.x) {
-    int4 q[kSortILP];
+  constexpr int kILP = kSortILP / 2;
+  for (int rb = threadIdx.x; rb < nrec; rb += kILP * blockDim.x) {
+    int4 q[kILP];
 #pragma unroll
-    for (int e = 0; e < kSortILP; ++e) {
+    for (int e = 0; e < kILP; ++e) {
       const int r = rb + e * blockDim.x;
       q[e] = r < nrec ? brec[base + r] : make_int4(0, 0, -1, 0);
     }
 #pragma unroll
-    for (int e = 0; e < kSortILP; ++e) {
-      if (q[e].z < 0) continue;
+    for (int e = 0; e < kILP; ++e) {
+      // a record outside the bucket cannot come from the scatter; skip it
+      // rather than index outside the histogram
+      if (q[e].z < p0 || q[e].z - p0 >= width) continue;
       const int rank = atomicAdd(&hs[q[e].z - p0], 1);
-      if (staged) stage[rb + e * blockDim.x] = make_int4(q[e].x, q[e].y, q[e].z, rank);
+      if (staged) {
+        const int r = rb + e * blockDim.x;
+        st_t[r] = q[e].x;
+        st_k[r] = q[e].y;
+        st_p[r] = q[e].z;
+        st_r[r] = rank;
+      }
     }
   }
   __syncthreads();
@@ -492,27 +510,40 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(const int4 *__rest
   }
   __syncthreads();
   if (staged) {
-    for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
-      const int4 q = stage[r];
-      src[hs[q.z - p0] + q.w] = r;
+    // slot of record r: its pixel's first slot plus its rank; the ranks are
+    // read by all threads before any slot is written (src reuses st_r)
+    constexpr int kPer = (kSortStage + kSortThreads - 1) / kSortThreads;
+    int dst[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int r = threadIdx.x + q * kSortThreads;
+      const int pz = r < nrec ? st_p[r] - (int)p0 : -1;
+      dst[q] = pz >= 0 && pz < width ? hs[pz] + st_r[r] : -1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int r = threadIdx.x + q * kSortThreads;
+      if (r < nrec && dst[q] >= 0 && dst[q] < nrec) src[dst[q]] = r;
     }
     __syncthreads();
     for (int d = threadIdx.x; d < nrec; d += blockDim.x) {  // in order: coalesced
-      const int4 q = stage[src[d]];
-      rec[base + d] = make_int2(q.x, q.y);
-      rpix[base + d] = q.z;
+      const int r = src[d];
+      if (r < 0 || r >= nrec) continue;
+      rec[base + d] = make_int2(st_t[r], st_k[r]);
+      rpix[base + d] = st_p[r];
     }
   } else {
-    for (int rb = threadIdx.x; rb < nrec; rb += kSortILP * blockDim.x) {
-      int4 q[kSortILP];
+    for (int rb = threadIdx.x; rb < nrec; rb += kILP * blockDim.x) {
+      int4 q[kILP];
 #pragma unroll
-      for (int e = 0; e < kSortILP; ++e) {
+      for (int e = 0; e < kILP; ++e) {
         const int r = rb + e * blockDim.x;
         q[e] = r < nrec ? brec[base + r] : make_int4(0, 0, -1, 0);
       }
 #pragma unroll
-      for (int e = 0; e < kSortILP; ++e) {
-        if (q[e].z < 0) continue;
+      for (int e = 0; e < kILP; ++e) {
+        if (q[e].z < p0 || q[e].z - p0 >= width) continue;
         const int pos = base + atomicAdd(&hs[q[e].z - p0], 1);
         rec[pos] = make_int2(q[e].x, q[e].y);
         rpix[pos] = q[e].z;
@@ -1236,7 +1267,11 @@ template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
+  if (e != cudaSuccess) return e;
+  // without the opt-in a block may use 48 KB of static and dynamic memory together
+  cudaFuncAttributes a{};
+  e = cudaFuncGetAttributes(&a, reinterpret_cast<const void *>(k));
+  if (e != cudaSuccess || a.sharedSizeBytes + bytes <= 48 * 1024) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -1438,18 +1473,22 @@ int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total
     return 0;
   }
   const int tiles = (int)((ev.n + per_tile - 1) / per_tile);
-  const size_t scatter_sm = (size_t)per_tile * (sizeof(int4) + sizeof(int));
-  const size_t sort_sm = ((((size_t)1 << shift) + 3) & ~(size_t)3) * sizeof(int) +
-                         (size_t)kSortStage * (sizeof(int4) + sizeof(int));
+  const size_t scatter_sm = (size_t)per_tile * 3 * sizeof(int);
+  const size_t sort_sm = (((size_t)1 << shift) + (size_t)kSortStage * 4) * sizeof(int);
   if (set_smem(k_bucket_scatter, scatter_sm) != cudaSuccess ||
       set_smem(k_bucket_sort, sort_sm) != cudaSuccess)
     return -1;
   const int scan_threads = std::min(1024, ((tiles + 3) / 4 + 31) / 32 * 32);
+  // each kernel consumes the previous one's output: stop at a failed launch
   k_bucket_count<<<tiles, kSortThreads, 0, s>>>(ev, g, shift, nb, (int)per_tile, bhist, err,
                                                zero_flow);
-  k_bucket_scan<<<nb, scan_threads, 0, s>>>(bhist, nb, tiles, btot);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  int *bpre = bhist + (size_t)nb * tiles;
+  k_bucket_scan<<<nb, scan_threads, 0, s>>>(bhist, nb, tiles, bpre, btot);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
   k_bucket_scatter<<<tiles, kSortThreads, scatter_sm, s>>>(ev, g, shift, nb, (int)per_tile, bhist,
-                                                          btot, brec);
+                                                          bpre, btot, brec);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
   k_bucket_sort<<<nb, kSortThreads, sort_sm, s>>>(brec, shift, nb, P, btot, cnt, total, rec, rpix);
   return cudaPeekAtLastError() == cudaSuccess ? 4 : -1;
 }

@@ -506,7 +506,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(dalloc(&c->total, 1));
   {  // a call's geometry is at most the context's, so at most min(P, max) buckets
     const size_t nbmax = std::min<size_t>(P, (size_t)bucket_sort_max_buckets());
-    VK_TRY(dalloc(&c->bhist, nbmax * bucket_sort_max_tiles()));
+    VK_TRY(dalloc(&c->bhist, 2 * nbmax * bucket_sort_max_tiles()));  // counts, then prefixes
     VK_TRY(dalloc(&c->btot, nbmax));
   }
   VK_TRY(dalloc(&c->err, 1));

@@ -74,8 +74,9 @@ int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *
 // bucket sort without global atomics.  bucket_sort_shift: log2 of the pixels
 // per bucket for P pixels, or -1 when P is beyond the form's limits
 // (launch_bucket_sort returns -1 outside bucket_sort_fits).  A geometry of P pixels has at most
-// min(P, bucket_sort_max_buckets()) buckets.  brec: n records; bhist: that
-// many buckets times bucket_sort_max_tiles() ints; btot: one per bucket.
+// min(P, bucket_sort_max_buckets()) buckets.  brec: n records; bhist: twice
+// that many buckets times bucket_sort_max_tiles() ints (per-tile counts,
+// then their prefixes); btot: one per bucket.
 int bucket_sort_shift(int64_t P);
 int bucket_sort_max_buckets();
 int bucket_sort_max_tiles();
