@@ -2,11 +2,13 @@
 //
 // Pipeline for one slice (Algorithm 1 with the pooling reformulation of
 // Eq. 13-17, Section 2.2.2):
-//   1. k_hist     PixelCount[p] += 1 for every event.
-//   2. k_scan_*   exclusive prefix sum of the counts: each pixel's segment in
-//                 a pixel-sorted event order.
-//   3. k_place    counting-sort placement of a record (t - t_ref, k) for every
-//                 event into its pixel's segment.
+//   1-3. sort by pixel: PixelCount[p] and a record (t - t_ref, k) for every
+//                 event in its pixel's segment of a pixel-sorted order.  The
+//                 bucket form (k_bucket_*, below) where the geometry and
+//                 event count allow it, else:
+//     1. k_hist     PixelCount[p] += 1 for every event.
+//     2. k_scan_*   exclusive prefix sum of the counts: each pixel's segment.
+//     3. k_place    counting-sort placement of each record into its segment.
 //   4. k_pixsum   PixelEmbed[p] = sum over the segment of exp(i t T/dt), in
 //                 record chunks of equal size; plain stores inside a chunk,
 //                 vector reductions only for the two pixels at its ends.
