@@ -39,10 +39,12 @@ struct veckm_ctx {
   int capture_grid = -1;
   bool capture_zeroed = false;
   int64_t capture_units = 0;
-  // Side stream for the window counts of the dense path (they need only the
-  // histogram), forked from and joined back to the caller's stream.
+  // Side stream of the dense path, forked from and joined back to the
+  // caller's stream: the clear of the pixel-sum grid (when no grid is known
+  // to be zero) under the sort, and the window counts (which need only the
+  // per-pixel counts) under the pixel sums and row pass.
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork0 = nullptr, ev_zero = nullptr, ev_fork = nullptr, ev_join = nullptr;
   int *cnt = nullptr, *cnt_tmp = nullptr, *ncnt = nullptr, *err = nullptr;
   int *off = nullptr, *cur = nullptr, *bsum = nullptr, *total = nullptr;
   // pixel-sorted event records (grown on demand), and the bucket sort's

@@ -313,17 +313,39 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
     return VECKM_OK;
   }
   // 6. the window's grid, pooling, then the packet's outputs
+  int r;
+  // the window counts on the context's side stream, under the conversion and
+  // the row pass; joined before the column pass (on every return once forked)
+  struct Join {
+    cudaStream_t s;
+    cudaEvent_t ev;
+    bool armed = false;
+    ~Join() {
+      if (armed) cudaStreamWaitEvent(s, ev, 0);
+    }
+  } join{cs, c->ev_join};
+  {
+    cudaError_t fe = cudaEventRecord(c->ev_fork, cs);
+    if (fe == cudaSuccess) fe = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (fe != cudaSuccess) return fail_cuda(fe, "forking the window counts");
+    r = launch_counts(g, s->cnt, c->cnt_tmp, c->ncnt, c->side);
+    fe = cudaEventRecord(c->ev_join, c->side);
+    join.armed = true;
+    if (r < 0 || fe != cudaSuccess) return fail_cuda(cudaGetLastError(), "window count launch");
+    launches += r;
+  }
   const long long P = (long long)g.W * g.H;
   k_fixed_to_float_dirty<<<(unsigned)std::min<long long>((P + 255) / 256, (long long)num_sms() * 8),
                            256, 0, cs>>>(s->acc64, s->accf, s->dirty, P, g.U);
   launches += 1;
   const Tables tb = c->tables();
   const Tune tn = c->tune_for(g);
-  int r;
   if ((r = launch_pool_rows(g, tb, s->accf, c->hbuf, cs, tn)) < 0) return fail_cuda(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
-  if ((r = launch_counts(g, s->cnt, c->cnt_tmp, c->ncnt, cs)) < 0) return fail_cuda(cudaGetLastError(), "window count launch");
-  launches += r;
+  if (join.armed) {
+    cudaStreamWaitEvent(cs, c->ev_join, 0);
+    join.armed = false;
+  }
   const Events ev{s->rx, s->ry, s->rt, s->cap, 0u, 0xffffffffu};
   const bool half_grid = predict && (c->flags & VECKM_ACC_FP16);
   r = half_grid ? launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, cs, tn)

@@ -116,6 +116,8 @@ void free_all(veckm_ctx *c) {
   if (c->tab_copied) cudaEventDestroy(c->tab_copied);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_fork0) cudaEventDestroy(c->ev_fork0);
+  if (c->ev_zero) cudaEventDestroy(c->ev_zero);
   if (c->side) cudaStreamDestroy(c->side);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   for (auto &v : c->pending)
@@ -214,6 +216,52 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
                                     (c->path == VECKM_PATH_AUTO && t_direct < t_dense));
   c->last_path = direct ? VECKM_PATH_DIRECT : VECKM_PATH_DENSE;
   mark();
+  // Side-stream work is forked with an event record and joined back before
+  // its consumer, on every return once forked.
+  struct Join {
+    cudaStream_t s;
+    cudaEvent_t ev;
+    bool armed = false;
+    void wait() {
+      if (armed) cudaStreamWaitEvent(s, ev, 0);
+      armed = false;
+    }
+    ~Join() { wait(); }
+  };
+  auto fork = [&](cudaEvent_t at) {
+    cudaError_t fe = cudaEventRecord(at, s);
+    if (fe == cudaSuccess) fe = cudaStreamWaitEvent(c->side, at, 0);
+    return fe;
+  };
+  // Dense path: the sums go to a grid known to be zero when there is one
+  // (the previous call's tensor-core head cleared it); otherwise acc is
+  // cleared, on the side stream under the sort.  The row pass writes the
+  // other grid, the column pass writes back into the first, which the gather
+  // reads.  A graph capture cannot know what runs before a replay: it clears,
+  // unless the plan capturing it picks the grid (capture_grid) and chooses
+  // between its two graphs at each launch.
+  const int64_t units = (int64_t)P * g.U;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "capture query");
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  const int zgrid = capturing ? c->capture_grid
+                              : (c->zero_grid >= 0 && c->zero_units >= units ? c->zero_grid : -1);
+  const bool known_zero = zgrid >= 0;
+  const bool may_zero = !capturing || c->capture_grid >= 0;
+  float4 *gsum = c->acc, *grow = c->hbuf;
+  if (zgrid == 1) std::swap(gsum, grow);
+  Join zjoin{s, c->ev_zero};
+  if (!direct) {
+    c->zero_grid = -1;
+    c->capture_zeroed = false;
+    if (!known_zero) {
+      cudaError_t fe = fork(c->ev_fork0);
+      if (fe == cudaSuccess) fe = cudaMemsetAsync(gsum, 0, (size_t)units * sizeof(float4), c->side);
+      if (fe == cudaSuccess) fe = cudaEventRecord(c->ev_zero, c->side);
+      zjoin.armed = true;
+      if (fe != cudaSuccess) return cuda_fail(fe, "clearing the pixel sums");
+    }
+  }
   // Sort by pixel: the bucket form (no global atomics) where the geometry
   // fits its limits, else histogram, scan and placement with global cursors.
   // Both give the per-pixel counts, the record total (off[P]) and the
@@ -235,22 +283,12 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
       return cuda_fail(cudaGetLastError(), "scan launch");
     launches += r;
   }
-  // The window counts need only the histogram: on the dense path they run on
-  // the side stream, under the placement, pixel sums and row pass, and join
-  // before the column pass (on every return once forked).
-  struct Join {
-    veckm_ctx *c;
-    cudaStream_t s;
-    bool armed = false;
-    void wait() {
-      if (armed) cudaStreamWaitEvent(s, c->ev_join, 0);
-      armed = false;
-    }
-    ~Join() { wait(); }
-  } join{c, s};
+  // The window counts need only the per-pixel counts: on the dense path they
+  // run on the side stream, under the pixel sums and row pass, and join
+  // before the column pass.
+  Join join{s, c->ev_join};
   if (!direct) {
-    cudaError_t fe = cudaEventRecord(c->ev_fork, s);
-    if (fe == cudaSuccess) fe = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    cudaError_t fe = fork(c->ev_fork);
     if (fe != cudaSuccess) return cuda_fail(fe, "forking the window counts");
     r = launch_counts(g, c->cnt, c->cnt_tmp, c->ncnt, c->side);
     fe = cudaEventRecord(c->ev_join, c->side);
@@ -283,25 +321,8 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     c->last_launches = launches;
     return VECKM_OK;
   }
-  // The sums go to a grid known to be zero when there is one (the previous
-  // call's tensor-core head cleared it); otherwise acc is cleared first.  The
-  // row pass writes the other grid, the column pass writes back into the
-  // first, which the gather reads.  A graph capture cannot know what runs
-  // before a replay: it clears, unless the plan capturing it picks the grid
-  // (capture_grid) and chooses between its two graphs at each launch.
-  const int64_t units = (int64_t)P * g.U;
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "capture query");
-  const bool capturing = cap != cudaStreamCaptureStatusNone;
-  const int zgrid = capturing ? c->capture_grid
-                              : (c->zero_grid >= 0 && c->zero_units >= units ? c->zero_grid : -1);
-  const bool known_zero = zgrid >= 0;
-  const bool may_zero = !capturing || c->capture_grid >= 0;
-  float4 *gsum = c->acc, *grow = c->hbuf;
-  if (zgrid == 1) std::swap(gsum, grow);
-  c->zero_grid = -1;
-  c->capture_zeroed = false;
-  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, !known_zero)) < 0)
+  zjoin.wait();  // the clear of gsum (side stream)
+  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, false)) < 0)
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
   mark();
@@ -481,6 +502,8 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   VK_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   VK_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  VK_TRY(cudaEventCreateWithFlags(&c->ev_fork0, cudaEventDisableTiming));
+  VK_TRY(cudaEventCreateWithFlags(&c->ev_zero, cudaEventDisableTiming));
   VK_TRY(dalloc(&c->tx, ((size_t)g.W + cfg->dx) * g.U));
   VK_TRY(dalloc(&c->sx, (size_t)g.U));
   VK_TRY(dalloc(&c->sy, (size_t)g.U));
