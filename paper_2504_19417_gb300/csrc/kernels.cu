@@ -61,6 +61,19 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 
+// a + b as two packed FP32x2 additions (the same roundings as add4)
+__device__ __forceinline__ float4 add4x2(float4 a, float4 b) {
+  uint64_t lo, hi;
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(lo)
+      : "l"(*reinterpret_cast<const uint64_t *>(&a.x)), "l"(*reinterpret_cast<const uint64_t *>(&b.x)));
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(hi)
+      : "l"(*reinterpret_cast<const uint64_t *>(&a.z)), "l"(*reinterpret_cast<const uint64_t *>(&b.z)));
+  const float2 l = *reinterpret_cast<const float2 *>(&lo), h = *reinterpret_cast<const float2 *>(&hi);
+  return make_float4(l.x, l.y, h.x, h.y);
+}
+
 // Two complex products: (a.x + i a.y)(b.x + i b.y) and (a.z + i a.w)(b.z + i b.w).
 __device__ __forceinline__ float4 cmul2(float4 a, float4 b) {
   return make_float4(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x),
@@ -612,21 +625,25 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
         tn = lane < r1 - c - 32 ? (uint32_t)__ldg(&rec[c + 32 + lane].x) : 0u;
         pn = lane < r1 - c - 32 ? __ldg(rpix + c + 32 + lane) : 0;
       }
+      // bit j: record j starts a pixel (differs from record j - 1, or from
+      // the running pixel for j = 0)
+      int prev = __shfl_up_sync(kFull, pl, 1);
+      if (lane == 0) prev = sp;
+      const unsigned starts = __ballot_sync(kFull, lane < m && pl != prev);
 #pragma unroll 4
       for (int j = 0; j < m; ++j) {
-        const int pj = __shfl_sync(kFull, pl, j);
         const uint32_t tj = __shfl_sync(kFull, tl, j);
-        if (pj != sp) {
+        if ((starts >> j) & 1u) {
           if (sp >= 0) {
             write(first);
             first = false;
           }
-          sp = pj;
+          sp = __shfl_sync(kFull, pl, j);
 #pragma unroll
           for (int v = 0; v < DV; ++v) s[v] = f4zero();
         }
 #pragma unroll
-        for (int v = 0; v < DV; ++v) s[v] = add4(s[v], time_phase2(tj, w[v][0], w[v][1]));
+        for (int v = 0; v < DV; ++v) s[v] = add4x2(s[v], time_phase2_lean(tj, w[v][0], w[v][1]));
       }
     }
     if (sp >= 0) write(true);
