@@ -1,8 +1,9 @@
 // Perceptron on the 5th-generation tensor cores, fused with the gather.
 //
-// Warp-specialised pipeline, two CTAs per SM, each with two 128-event tiles
-// in flight:
-//   - 8 producer warps gather the rows of a tile, P[p] * conj(exp(i t T/dt))
+// Warp-specialised pipeline, each CTA with two 128-event tiles in flight
+// (D = 64: two CTAs per SM with 8 producer warps each; D = 128: one CTA
+// per SM, whose operand tiles fill shared memory, with 16 producer warps):
+//   - producer warps gather the rows of a tile, P[p] * conj(exp(i t T/dt))
 //     (the pooled value at the event's pixel times the conjugate temporal
 //     phase, Eq. 16), straight into shared memory as BF16 (or FP16) in the
 //     K-major 128-byte-swizzled layout that tcgen05.mma reads: the tile is
@@ -57,11 +58,17 @@ namespace {
 
 constexpr int kM = 128;  // events per tile (MMA M)
 constexpr int kN = 128;  // hidden units (MMA N)
-constexpr int kProdWarps = 8;
 constexpr int kEpiWarps = 4;
+// Producer warps: 8 of 16 rows each for D = 64 (two CTAs of 12 warps per SM);
+// 16 of 8 rows each for D = 128, whose operand tiles allow one CTA per SM
+// (20 warps then keep the loads of more rows in flight)
+template <int DV>
+struct Shape {
+  static constexpr int prod = DV == 1 ? 8 : 16;
+  static constexpr int rows = 128 / prod;
+  static constexpr int threads = 32 * (4 + prod);
+};
 constexpr int kMmaWarp = 0;  // epilogue warp 0 also issues the MMAs
-constexpr int kThreads = 32 * (kEpiWarps + kProdWarps);
-constexpr int kRowsPerWarp = kM / kProdWarps;
 constexpr int kTmemCols = 2 * kN;  // two accumulators
 
 // Second-layer weights and first-layer bias, by value.
@@ -163,7 +170,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 template <int DV, bool HALF>
-__global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
+__global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     k_predict_tc(Events ev, const int64_t *__restrict__ K, int64_t nK,
                  const int2 *__restrict__ rec, const int *__restrict__ rpix,
                  const int *__restrict__ nsorted, Geometry g, Tables tb,
@@ -173,6 +180,8 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
   constexpr int U = 32 * DV;
   constexpr int IN = 4 * U;  // 2D, the MMA K extent
   constexpr int TILE_BYTES = kM * IN * 2;
+  constexpr int kProdWarps = Shape<DV>::prod;
+  constexpr int kRowsPerWarp = Shape<DV>::rows;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;                            // 2 x [128 x IN] half, SW128
@@ -223,7 +232,8 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
 
   if (warp >= kEpiWarps) {
     // ------------------------------------------------------------ producers
-    // Warp pw fills rows pw*16 .. pw*16+15 of every tile.  Lane l computes
+    // Warp pw fills rows pw*R .. pw*R+R-1 of every tile (R = kRowsPerWarp,
+    // 16 or 8).  Lane l computes
     // unit u = l + 32 v (channels 2u, 2u+1) of a row and stores its four
     // halves, Re(2u) Re(2u+1) Im(2u) Im(2u+1), as one 8-byte group at K
     // positions 4u..4u+3 (W1's columns are permuted to match on the host).
@@ -234,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
       wf[v][0] = __ldg(tb.wt + 2 * (lane + 32 * v));
       wf[v][1] = __ldg(tb.wt + 2 * (lane + 32 * v) + 1);
     }
-    // Byte offset of that group for row pw*16 + j: K-block u / 16 (bits 14+),
+    // Byte offset of that group for row pw*R + j: K-block u / 16 (bits 14+),
     // row group (bits 10+), row j % 8 (bits 7-9), 16-byte chunk (u / 2) % 8
     // XOR j % 8 (bits 4-6), half of the chunk u % 2 (bit 3).  For j % 8 == 0
     // that is lo[v]; for j % 8 == r it is lo[v] ^ (r * 0x90) (r into bits 7-9
@@ -244,7 +254,8 @@ __global__ void __launch_bounds__(kThreads, DV == 1 ? 2 : 1)
 #pragma unroll
     for (int v = 0; v < DV; ++v) {
       const uint32_t u = lane + 32 * v;
-      lo[v] = (u >> 4) * (kM * 128) + (uint32_t)pw * 2048 + (((u >> 1) & 7) << 4) + (u & 1) * 8;
+      lo[v] = (u >> 4) * (kM * 128) + (uint32_t)pw * (kRowsPerWarp * 128) + (((u >> 1) & 7) << 4) +
+              (u & 1) * 8;
     }
     // Row metadata of tile t for lane j < 16 (row pw*16 + j): the pixel whose
     // pooled vector is read, t - t_ref, 1 for a valid event (0 otherwise; the
@@ -549,7 +560,7 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
   const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (2 * kM) +
-                    sizeof(int) * 2 * kM + 8 * 6 + sizeof(int2) * kProdWarps * 2 * kRowsPerWarp +
+                    sizeof(int) * 2 * kM + 8 * 6 + sizeof(int2) * 2 * kM +
                     16 + 1024;  // + SW128 alignment slack
   auto kern = k_predict_tc<DV, HALF>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
@@ -557,6 +568,7 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
       cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return -1;
+  constexpr int kThreads = Shape<DV>::threads;
   int per_sm = std::min(blocks_per_sm((const void *)kern, kThreads, sm), 512 / kTmemCols);
   if (ctas_req > 0) per_sm = std::min(per_sm, ctas_req);
   const int64_t tiles = (nK + kM - 1) / kM;

@@ -284,9 +284,12 @@ def test_full_size_640x480_sampled(mode):
     _check_flow(flow[K], ref, w, mode)
 
 
-def test_full_size_1280x720_d128_sampled():
+@pytest.mark.parametrize("mode", [vk.MLP_BF16, vk.MLP_BF16 | vk.ACC_FP16, vk.MLP_FP16])
+def test_full_size_1280x720_d128_sampled(mode):
+    """The 1280x720, 4M-event, D=128 precision workload: FP32 and FP16 storage
+    of the pooled grid under a 256 -> 128 -> 2 head on the tensor cores."""
     sl, D = synth.workload("slice-1280x720-4M")
-    enc, TXY, w = make(sl, D, mode=vk.MLP_BF16)
+    enc, TXY, w = make(sl, D, mode=mode)
     x, y, t = to_dev(sl)
     flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
     emb = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
@@ -294,4 +297,4 @@ def test_full_size_1280x720_d128_sampled():
     K = np.sort(np.random.default_rng(12).choice(sl.n, 300, replace=False)).astype(np.int64)
     ref = _oracle_emb(sl, D, 10, 10, 16_000, TXY, K=K)
     assert emb_rel_err(emb[K], ref).max() <= EMB_TOL_FP32
-    _check_flow(flow[K], ref, w, vk.MLP_BF16)
+    _check_flow(flow[K], ref, w, mode)
