@@ -670,7 +670,7 @@ enum class Pass { Rows, Cols };
 template <int DV, Pass P, bool HALF = false>
 __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
-                                                 int seg, int nseg,
+                                                 int seg, int nseg, int up,
                                                  const int *__restrict__ ncnt = nullptr) {
   static_assert(!HALF || P == Pass::Cols, "FP16 output is written by the column pass");
   constexpr int U = 32 * DV;
@@ -690,8 +690,11 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   const int o0 = s * seg;
   const int nout = min(len, o0 + seg) - o0;
   const int in0 = o0 - r;
-  const size_t base = (P == Pass::Rows) ? (size_t)line * g.W * U : (size_t)line * U;
-  const size_t stride = (P == Pass::Rows) ? (size_t)U : (size_t)g.W * U;
+  // this warp's slice of each pixel: units u0 .. u0 + U - 1 of up (grids and
+  // tables are [pixel][up] units; the ring holds one slice)
+  const int u0 = blockIdx.y * U;
+  const size_t base = ((P == Pass::Rows) ? (size_t)line * g.W * up : (size_t)line * up) + u0;
+  const size_t stride = (P == Pass::Rows) ? (size_t)up : (size_t)g.W * up;
   const int nb = (nout + L - 1) / L;  // output blocks; input blocks 0..nb
 
   auto slot = [&](int b) { return ring + (size_t)(b % 3) * SL; };
@@ -712,10 +715,10 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
       const float4 *arow;
       if (P == Pass::Rows) {  // tx row of the block's first input column (halo rows from -dx)
         const int a = min(max(in0 + b * L, -g.dx), g.W - 1);
-        arow = tb.tx + (size_t)(a + g.dx) * U;
+        arow = tb.tx + (size_t)(a + g.dx) * up + u0;
       } else {  // ty row of the output block's first row
         const int a = min(o0 + b * L, g.H - 1);
-        arow = tb.ty + (size_t)a * U;
+        arow = tb.ty + (size_t)a * up + u0;
       }
 #pragma unroll
       for (int v = 0; v < DV; ++v) cp_async16(sl + L * U + lane + 32 * v, arow + lane + 32 * v);
@@ -740,11 +743,11 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   for (int v = 0; v < DV; ++v) {
     const int u = lane + 32 * v;
     if (P == Pass::Rows) {
-      fl[v] = __ldg(tb.ty + (size_t)line * U + u);
-      st[v] = __ldg(tb.sx + u);
+      fl[v] = __ldg(tb.ty + (size_t)line * up + u0 + u);
+      st[v] = __ldg(tb.sx + u0 + u);
     } else {
-      fl[v] = __ldg(tb.tx + (size_t)(line + g.dx) * U + u);
-      st[v] = __ldg(tb.sy + u);
+      fl[v] = __ldg(tb.tx + (size_t)(line + g.dx) * up + u0 + u);
+      st[v] = __ldg(tb.sy + u0 + u);
     }
   }
   auto modulate = [&](float4 *sl) {  // row pass: sl[q] *= tx[x0 + q] ty[y]
@@ -1323,14 +1326,16 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   // a warp walks `seg` outputs of one line (a whole number of windows)
   const int seg = L * (seg_windows > 0 ? seg_windows : std::max(1, (128 + L / 2) / L));
   const int nseg = (len + seg - 1) / seg;
-  const size_t per_warp = (size_t)3 * (L + 1) * 32 * DV * sizeof(float4);
+  // one warp per (line segment, 32-unit slice of the pixels): DV slices, so
+  // the ring of a warp holds 32 units per row whatever D is
+  const size_t per_warp = (size_t)3 * (L + 1) * 32 * sizeof(float4);
   int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
   if (wpb_req > 0 && wpb_req <= 4 && per_warp * wpb_req <= kBoxSmemMax) wpb = wpb_req;
   const size_t sm = per_warp * wpb;
-  if (set_smem(k_box_pass<DV, P, HALF>, sm) != cudaSuccess) return -1;
+  if (set_smem(k_box_pass<1, P, HALF>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
-  const int grid = (int)((warps + wpb - 1) / wpb);
-  k_box_pass<DV, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, ncnt);
+  const dim3 grid((unsigned)((warps + wpb - 1) / wpb), DV);
+  k_box_pass<1, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, 32 * DV, ncnt);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
