@@ -169,7 +169,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int DV, bool HALF>
+// Loads N consecutive ints of shared memory (16-byte aligned for N >= 4,
+// 8-byte aligned for N = 2) in N / 4 vector loads (one for N = 2).
+template <int N>
+__device__ __forceinline__ void lds_ints(const int *p, int (&o)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const int4 v = reinterpret_cast<const int4 *>(p)[i];
+      o[4 * i] = v.x, o[4 * i + 1] = v.y, o[4 * i + 2] = v.z, o[4 * i + 3] = v.w;
+    }
+  } else {
+    static_assert(N == 2, "rows per batch: 2 or a multiple of 4");
+    const int2 v = *reinterpret_cast<const int2 *>(p);
+    o[0] = v.x, o[1] = v.y;
+  }
+}
+
+// F16: the operands are FP16 (else BF16), fixed per launch.
+template <int DV, bool HALF, bool F16>
 __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     k_predict_tc(Events ev, const int64_t *__restrict__ K, int64_t nK,
                  const int2 *__restrict__ rec, const int *__restrict__ rpix,
@@ -189,11 +207,11 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
   float *sInv = reinterpret_cast<float *>(sB + TILE_BYTES);   // [2][128] 1 / window count
   int *sK = reinterpret_cast<int *>(sInv + 2 * kM);            // [2][128] output row codes
   uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 2 * kM);  // full[2], done[2], empty[2]
-  int2 *sMeta = reinterpret_cast<int2 *>(bars + 6);             // [8 warps][2][16]
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(sMeta + kProdWarps * 2 * kRowsPerWarp);
+  int *sMeta = reinterpret_cast<int *>(bars + 6);  // per producer warp [2][pixels R | t R]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sMeta + kProdWarps * 4 * kRowsPerWarp);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int fp16 = mlp.half_kind;
+  constexpr int fp16 = F16 ? 1 : 0;
 
   {  // W1 (already in SW128 order)
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
@@ -299,8 +317,17 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         outk = invalid_row(i);
       }
     };
-    // (pixel, t - t_ref) of this warp's rows, two tiles: [tile parity][16]
-    int2 *ms = sMeta + pw * 2 * kRowsPerWarp;
+    // pixels and t - t_ref of this warp's rows, two tiles: [tile parity]
+    // [pixel of rows 0..R-1 | t of rows 0..R-1], so that a batch's pixels (or
+    // times) come in one or two vector loads (16-byte aligned: the region
+    // starts 16-byte aligned and R is 8 or 16)
+    int *ms = sMeta + pw * 4 * kRowsPerWarp;
+    auto ms_put = [&](int par, int pix, uint32_t trel) {
+      if (lane < kRowsPerWarp) {
+        ms[par * 2 * kRowsPerWarp + lane] = pix;
+        ms[par * 2 * kRowsPerWarp + kRowsPerWarp + lane] = (int)trel;
+      }
+    };
     const uint32_t sA_a = smem_u32(sA);
     // FP16 grid: uint2 (half2 Re pair, half2 Im pair) per unit, already
     // divided by n; FP32 grid: float4 (re 2u, im 2u, re 2u+1, im 2u+1)
@@ -313,26 +340,34 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     static_assert(NB % 2 == 0, "batches alternate between two register sets");
     Q qa[kB][DV], qb[kB][DV];
     auto issue = [&](int par, int j0, Q(&q)[kB][DV]) {
+      constexpr int kC = kB < 4 ? kB : 4;  // pixels read per vector load
 #pragma unroll
-      for (int r = 0; r < kB; ++r) {
-        const int pj = ms[par * kRowsPerWarp + j0 + r].x;
+      for (int c = 0; c < kB; c += kC) {
+        int pj[kC];
+        lds_ints<kC>(ms + par * 2 * kRowsPerWarp + j0 + c, pj);
 #pragma unroll
-        for (int v = 0; v < DV; ++v) q[r][v] = __ldg(pooled + (size_t)pj * U + lane + 32 * v);
+        for (int r = 0; r < kC; ++r) {
+#pragma unroll
+          for (int v = 0; v < DV; ++v)
+            q[c + r][v] = __ldg(pooled + (size_t)pj[r] * U + lane + 32 * v);
+        }
       }
     };
     auto compute = [&](int par, int j0, const Q(&q)[kB][DV], uint32_t Abuf) {
       // every t of the batch first; plain stores let the rows interleave
-      uint32_t tjs[kB];
-#pragma unroll
-      for (int r = 0; r < kB; ++r) tjs[r] = (uint32_t)ms[par * kRowsPerWarp + j0 + r].y;
+      int tjs[kB];
+      lds_ints<kB>(ms + par * 2 * kRowsPerWarp + kRowsPerWarp + j0, tjs);
       uint8_t *Ag = sA + (Abuf - sA_a);
 #pragma unroll
       for (int r = 0; r < kB; ++r) {
         const int j = j0 + r;
-        const uint32_t tj = tjs[r];
+        const uint32_t tj = (uint32_t)tjs[r];
 #pragma unroll
         for (int v = 0; v < DV; ++v) {
-          const float4 ph = time_phase2(tj, wf[v][0], wf[v][1]);  // (c0, s0, c1, s1)
+          // (c0, s0, c1, s1); the lean form needs a register the FP16 grid's
+          // variant has no room for
+          const float4 ph = HALF ? time_phase2(tj, wf[v][0], wf[v][1])
+                                 : time_phase2_lean(tj, wf[v][0], wf[v][1]);
           uint32_t wre, wim;
           if constexpr (HALF) {
             // P conj(phase) in packed half2: Re = PR c + PI s, Im = PI c - PR s
@@ -375,7 +410,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       uint32_t trel;
       meta(blockIdx.x, pix, trel, c_inv, c_outk);
       if (!HALF && c_inv != 0.f) c_inv = 1.0f / (float)__ldg(ncnt + pix);
-      if (lane < kRowsPerWarp) ms[lane] = make_int2(pix, (int)trel);
+      ms_put(0, pix, trel);
       __syncwarp();
       issue(0, 0, qa);
       pf_load((int)(blockIdx.x + 2 * gridDim.x));
@@ -410,7 +445,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
           else issue(b, (h + 1) * kB, qb);
         } else if (has_next) {
           __syncwarp();
-          if (lane < kRowsPerWarp) ms[(b ^ 1) * kRowsPerWarp + lane] = make_int2(n_pix, (int)n_trel);
+          ms_put(b ^ 1, n_pix, n_trel);
           __syncwarp();
           issue(b ^ 1, 0, qa);
         }
@@ -550,7 +585,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
   }
 }
 
-template <int DV, bool HALF>
+template <int DV, bool HALF, bool F16>
 int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                     const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                     const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
@@ -562,7 +597,7 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (2 * kM) +
                     sizeof(int) * 2 * kM + 8 * 6 + sizeof(int2) * 2 * kM +
                     16 + 1024;  // + SW128 alignment slack
-  auto kern = k_predict_tc<DV, HALF>;
+  auto kern = k_predict_tc<DV, HALF, F16>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
           cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -599,19 +634,21 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
                       int *err, cudaStream_t s, const Tune &tn, float4 *zero_buf,
                       int64_t zero_units, bool *zeroed) {
-  const bool h = mlp.pooled_half != 0;
-#define VECKM_TC(DV_, H_)                                                                    \
-  predict_tc_impl<DV_, H_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, \
-                           tn.tc_ctas, zero_buf, zero_units, zeroed)
+  const bool h = mlp.pooled_half != 0, f16 = mlp.half_kind != 0;
+#define VECKM_TC(DV_, H_, F_)                                                                    \
+  predict_tc_impl<DV_, H_, F_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, \
+                               s, tn.tc_ctas, zero_buf, zero_units, zeroed)
+#define VECKM_TC2(DV_, H_) (f16 ? VECKM_TC(DV_, H_, true) : VECKM_TC(DV_, H_, false))
   if (zeroed) *zeroed = false;
   switch (g.U / 32) {
     case 1:
-      return h ? VECKM_TC(1, true) : VECKM_TC(1, false);
+      return h ? VECKM_TC2(1, true) : VECKM_TC2(1, false);
     case 2:
-      return h ? VECKM_TC(2, true) : VECKM_TC(2, false);
+      return h ? VECKM_TC2(2, true) : VECKM_TC2(2, false);
     default:
       return -1;  // 2D > 256 does not fit the operand tiles in shared memory
   }
+#undef VECKM_TC2
 #undef VECKM_TC
 }
 
