@@ -284,7 +284,11 @@ __global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__res
 //   d. k_bucket_sort: per bucket, a counting sort of its records by pixel in
 //      shared memory, written out in order (buckets above kSortStage records
 //      place them straight into the bucket's region instead); also writes
-//      the pixel counts.
+//      the pixel counts.  With a grid given, it also zeroes the rows of the
+//      pixels at the edges of the per-pixel sums' record ranges (the sorted
+//      positions c * kPixRecs and c * kPixRecs + kPixRecs - 1), the only
+//      pixels those sums add into rather than store: the sums then need no
+//      cleared grid.
 // Records of one pixel come out in no particular order, as with k_place.
 constexpr int kSortThreads = 512;
 constexpr int kMaxBuckets = 1024;
@@ -292,6 +296,9 @@ constexpr int kMaxBucketShift = 15;  // 32768 pixels: a 128 KB shared histogram
 constexpr int kMaxSortTiles = 4096;
 constexpr int kSortILP = 8;        // events or records in flight per thread
 constexpr int kSortStage = 4096;   // records a bucket sorts in shared memory
+// Records per warp in the per-pixel sums (k_pixsum): measured on GB300
+// against 64 to 256 and against one wave of longer ranges.
+constexpr int kPixRecs = 128;
 
 // Exclusive prefix of v[0..nb) into out[0..nb) (out may be v) and the sum in
 // *total, for nb <= 2 * blockDim.x (one block; s_warp holds 33 ints).
@@ -456,7 +463,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_sort(const int4 *__r
                                                               int *__restrict__ cnt,
                                                               int *__restrict__ total_out,
                                                               int2 *__restrict__ rec,
-                                                              int *__restrict__ rpix) {
+                                                              int *__restrict__ rpix,
+                                                              float4 *__restrict__ zgrid,
+                                                              int zunits) {
   extern __shared__ int hs[];
   const int width = 1 << shift;
   // staged records as three int arrays (t - t_ref, index, pixel) and each
@@ -566,18 +575,43 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_sort(const int4 *__r
     }
   }
   if (b == nb - 1 && threadIdx.x == 0) *total_out = base + nrec;
+  if (zgrid && nrec > 0) {
+    // rows of the pixels at range edges inside [base, base + nrec): one warp
+    // per range, lanes over the row's units.  Their pixels are read back from
+    // the slots just written (shared memory when staged, else this block's
+    // own global writes, visible after the barrier)
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c0 = base / kPixRecs, c1 = ((int64_t)base + nrec - 1) / kPixRecs;
+    for (int64_t c = c0 + warp; c <= c1; c += blockDim.x >> 5) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t pos = c * kPixRecs + (e ? kPixRecs - 1 : 0);
+        if (pos < base || pos >= (int64_t)base + nrec) continue;
+        int p = -1;
+        if (staged) {
+          const int r = src[pos - base];
+          if (r >= 0 && r < nrec) p = st_p[r];
+        } else {
+          p = rpix[pos];
+        }
+        if (p < p0 || p - p0 >= width || p >= P) continue;
+        for (int u = lane; u < zunits; u += 32) zgrid[(size_t)p * zunits + u] = f4zero();
+      }
+    }
+  }
 }
 
 // 4. per-pixel phase sums PixelEmbed[p] = sum over the pixel's records of
-// exp(i t T/dt), into an accumulator cleared beforehand (empty pixels stay
-// zero).  Work is balanced by records: warp c takes records
+// exp(i t T/dt).  Work is balanced by records: warp c takes records
 // [c*recs, (c+1)*recs) in pixel-sorted order, streams them in groups of 32
 // (t and pixel, the next group loading while one is summed), and writes each
 // pixel's sum when the pixel changes -
 // a plain store for pixels that lie wholly inside its range, a vector
-// reduction for the first and last pixel, which may continue in a
-// neighbouring warp's range.
-constexpr int kPixRecs = 128;
+// reduction for the first pixel and, unless the range is the last, the last
+// pixel, which may continue in a neighbouring warp's range.  Only those
+// pixels must be zero beforehand (the bucket sort can zero exactly them);
+// pixels without records are not written at all.
 
 __device__ __forceinline__ void red_add_v4(float4 *p, float4 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
@@ -646,7 +680,9 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
         for (int v = 0; v < DV; ++v) s[v] = add4x2(s[v], time_phase2_lean(tj, w[v][0], w[v][1]));
       }
     }
-    if (sp >= 0) write(true);
+    // the last range's last pixel, when it started inside the range, has no
+    // other contributor
+    if (sp >= 0) write(first || r1 < ns);
   }
 }
 
@@ -667,11 +703,15 @@ enum class Pass { Rows, Cols };
 // HALF (column pass only): the output is divided by the pixel's window count
 // n (Eq. 17; 0 where the window is empty) and stored as FP16, unit u of a
 // pixel = 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
+// occ (row pass, window length L <= 32): per-pixel event counts; pixels with
+// none are taken as zero without reading src, whose rows there may hold
+// anything.
 template <int DV, Pass P, bool HALF = false>
 __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
                                                  int seg, int nseg, int up,
-                                                 const int *__restrict__ ncnt = nullptr) {
+                                                 const int *__restrict__ ncnt = nullptr,
+                                                 const int *__restrict__ occ = nullptr) {
   static_assert(!HALF || P == Pass::Cols, "FP16 output is written by the column pass");
   constexpr int U = 32 * DV;
   extern __shared__ float4 smem[];
@@ -698,15 +738,31 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   const int nb = (nout + L - 1) / L;  // output blocks; input blocks 0..nb
 
   auto slot = [&](int b) { return ring + (size_t)(b % 3) * SL; };
+  // row pass with occ: lane q holds the count of pixel q of the next block to
+  // issue, loaded one block ahead of its use
+  const bool use_occ = P == Pass::Rows && occ != nullptr && L <= 32;
+  int occ_v = 0;
+  auto load_occ = [&](int b) {
+    const int pos = in0 + b * L + lane;
+    occ_v = (b <= nb && lane < L && pos >= 0 && pos < len)
+                ? __ldg(occ + (size_t)line * g.W + pos) : 0;
+  };
+  if (use_occ) load_occ(0);
   auto issue = [&](int b) {  // input block b and its anchor row -> its slot (one group)
     if (b <= nb) {
       float4 *sl = slot(b);
+      unsigned on = ~0u;  // bit q: pixel q of the block is read
+      if (use_occ) {
+        on = __ballot_sync(kFull, occ_v != 0);
+        load_occ(b + 1);
+      }
       for (int q = 0; q < L; ++q) {
         const int pos = in0 + b * L + q;
+        const bool rd = pos >= 0 && pos < len && ((on >> (q & 31)) & 1u);
 #pragma unroll
         for (int v = 0; v < DV; ++v) {
           const int u = lane + 32 * v;
-          if (pos >= 0 && pos < len)
+          if (rd)
             cp_async16(sl + q * U + u, src + base + (size_t)pos * stride + u);
           else
             sl[q * U + u] = f4zero();
@@ -1304,8 +1360,6 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
   if (clear && cudaMemsetAsync(acc, 0, (size_t)P * g.U * sizeof(float4), s) != cudaSuccess)
     return -1;
   if (n == 0) return 0;
-  // 128 records per warp: measured on GB300 against 64 to 256 and against
-  // one wave of longer ranges (the window counts share the SMs meanwhile)
   const int64_t recs = kPixRecs;
   const int64_t warps = (n + recs - 1) / recs;
   const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
@@ -1318,7 +1372,7 @@ constexpr size_t kBoxSmemMax = 200 * 1024;
 
 template <int DV, Pass P, bool HALF = false>
 int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s,
-             const int *ncnt, int seg_windows, int wpb_req) {
+             const int *ncnt, int seg_windows, int wpb_req, const int *occ = nullptr) {
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
   const int L = 2 * r + 1;
   const int len = (P == Pass::Rows) ? g.W : g.H;
@@ -1335,7 +1389,8 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   if (set_smem(k_box_pass<1, P, HALF>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const dim3 grid((unsigned)((warps + wpb - 1) / wpb), DV);
-  k_box_pass<1, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, 32 * DV, ncnt);
+  k_box_pass<1, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, 32 * DV, ncnt,
+                                                    occ);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -1484,7 +1539,7 @@ bool bucket_sort_fits(int64_t P, int64_t n) {
 
 int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total, int2 *rec,
                        int *rpix, int4 *brec, int *bhist, int *btot, int *err, float *zero_flow,
-                       cudaStream_t s) {
+                       cudaStream_t s, float4 *zgrid) {
   const int64_t P = (int64_t)g.W * g.H;
   const int shift = bucket_sort_shift(P);
   const int64_t per_tile = bucket_sort_tile(ev.n);
@@ -1513,7 +1568,8 @@ int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total
   k_bucket_scatter<<<tiles, kSortThreads, scatter_sm, s>>>(ev, g, shift, nb, (int)per_tile, bhist,
                                                           bpre, btot, brec);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_bucket_sort<<<nb, kSortThreads, sort_sm, s>>>(brec, shift, nb, P, btot, cnt, total, rec, rpix);
+  k_bucket_sort<<<nb, kSortThreads, sort_sm, s>>>(brec, shift, nb, P, btot, cnt, total, rec, rpix,
+                                                  zgrid, g.U);
   return cudaPeekAtLastError() == cudaSuccess ? 4 : -1;
 }
 
@@ -1538,9 +1594,10 @@ int launch_direct(const Events &ev, const int64_t *K, int64_t nK, const Geometry
 }
 
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
-                     cudaStream_t s, const Tune &tn) {
+                     cudaStream_t s, const Tune &tn, const int *occ) {
+  if (occ && 2 * g.dx + 1 > 32) return -1;  // the occupancy mask covers one warp's lanes
   VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Rows>(g, tb, acc, hbuf, s, nullptr, tn.rows_seg,
-                                                   tn.rows_wpb)));
+                                                   tn.rows_wpb, occ)));
 }
 
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,

@@ -233,13 +233,20 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     if (fe == cudaSuccess) fe = cudaStreamWaitEvent(c->side, at, 0);
     return fe;
   };
-  // Dense path: the sums go to a grid known to be zero when there is one
-  // (the previous call's tensor-core head cleared it); otherwise acc is
-  // cleared, on the side stream under the sort.  The row pass writes the
-  // other grid, the column pass writes back into the first, which the gather
-  // reads.  A graph capture cannot know what runs before a replay: it clears,
-  // unless the plan capturing it picks the grid (capture_grid) and chooses
-  // between its two graphs at each launch.
+  // Dense path: with the bucket sort (and a window of at most 32 columns) the
+  // pixel sums need no cleared grid: the sort zeroes the rows of the pixels
+  // at the edges of the sums' record ranges, the only ones the sums add
+  // into, the sums store the other pixels that have records, and the row
+  // pass reads only pixels that have records (occupancy from the counts).
+  // Otherwise the sums go to a grid known to be zero when there is one (the
+  // previous call's tensor-core head cleared it), else acc is cleared, on the
+  // side stream under the sort.  The row pass writes the other grid, the
+  // column pass writes back into the first, which the gather reads.  A graph
+  // capture cannot know what runs before a replay: it clears, unless the plan
+  // capturing it picks the grid (capture_grid) and chooses between its two
+  // graphs at each launch.
+  const bool bucketed = bucket_sort_fits((int64_t)P, n);
+  const bool sparse_rows = bucketed && 2 * g.dx + 1 <= 32;
   const int64_t units = (int64_t)P * g.U;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "capture query");
@@ -254,7 +261,7 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   if (!direct) {
     c->zero_grid = -1;
     c->capture_zeroed = false;
-    if (!known_zero) {
+    if (!known_zero && !sparse_rows) {
       cudaError_t fe = fork(c->ev_fork0);
       if (fe == cudaSuccess) fe = cudaMemsetAsync(gsum, 0, (size_t)units * sizeof(float4), c->side);
       if (fe == cudaSuccess) fe = cudaEventRecord(c->ev_zero, c->side);
@@ -267,10 +274,10 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   // Both give the per-pixel counts, the record total (off[P]) and the
   // pixel-grouped records.
   float *zero_flow = (sorted && !direct) ? out : nullptr;
-  const bool bucketed = bucket_sort_fits((int64_t)P, n);
   if (bucketed) {
     if ((r = launch_bucket_sort(ev, g, c->cnt, c->off + P, c->rec, c->rpix, c->brec, c->bhist,
-                                c->btot, c->err, zero_flow, s)) < 0)
+                                c->btot, c->err, zero_flow, s,
+                                sparse_rows && !direct ? gsum : nullptr)) < 0)
       return cuda_fail(cudaGetLastError(), "bucket sort launch");
     launches += r;
   } else {
@@ -326,7 +333,7 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
   mark();
-  if ((r = launch_pool_rows(g, tb, gsum, grow, s, tn)) < 0)
+  if ((r = launch_pool_rows(g, tb, gsum, grow, s, tn, sparse_rows ? c->cnt : nullptr)) < 0)
     return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   mark();
@@ -347,9 +354,10 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     MLP m = c->mlp();
     m.pooled_half = half_grid ? 1 : 0;
     bool zeroed = false;
+    // a cleared grid serves only a next call whose sums cannot do without one
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
                           c->off + P, g, tb, gsum, c->ncnt, m, out, c->err, s, tn,
-                          may_zero ? grow : nullptr, units, &zeroed);
+                          may_zero && !sparse_rows ? grow : nullptr, units, &zeroed);
     if (r >= 0 && zeroed && !capturing) {
       c->zero_grid = grow == c->acc ? 0 : 1;
       c->zero_units = units;

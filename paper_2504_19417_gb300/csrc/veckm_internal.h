@@ -76,7 +76,11 @@ int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *
 // (launch_bucket_sort returns -1 outside bucket_sort_fits).  A geometry of P pixels has at most
 // min(P, bucket_sort_max_buckets()) buckets.  brec: n records; bhist: twice
 // that many buckets times bucket_sort_max_tiles() ints (per-tile counts,
-// then their prefixes); btot: one per bucket.
+// then their prefixes); btot: one per bucket.  zgrid (optional): a grid of
+// g.U float4 per pixel whose rows at the per-pixel sums' range edges are
+// zeroed, so that launch_pixsum(..., clear = false) may write into it
+// uncleared (pixels without records then hold stale values: read it only
+// through launch_pool_rows with occ = the counts).
 int bucket_sort_shift(int64_t P);
 int bucket_sort_max_buckets();
 int bucket_sort_max_tiles();
@@ -84,16 +88,19 @@ int bucket_sort_max_tiles();
 bool bucket_sort_fits(int64_t P, int64_t n);
 int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total, int2 *rec,
                        int *rpix, int4 *brec, int *bhist, int *btot, int *err, float *zero_flow,
-                       cudaStream_t s);
-// Clears acc (unless the caller knows it is zero: clear = false), then sums
-// the *nsorted pixel-sorted records (n bounds it).
+                       cudaStream_t s, float4 *zgrid = nullptr);
+// Clears acc (unless the caller knows it is zero, or the sort zeroed the
+// range-edge rows: clear = false), then sums the *nsorted pixel-sorted
+// records (n bounds it).  Pixels without records are not written.
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
                   const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear = true);
 // Blocks of `threads` threads with `smem` dynamic bytes that fit on one SM.
 int blocks_per_sm(const void *func, int threads, size_t smem);
 // Pooling: row pass acc -> hbuf, column pass hbuf -> acc, window counts.
+// occ (row pass; window length 2dx+1 <= 32, else -1): per-pixel event counts,
+// pixels with none read as zero whatever acc holds there.
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
-                     cudaStream_t s, const Tune &tn = Tune{});
+                     cudaStream_t s, const Tune &tn = Tune{}, const int *occ = nullptr);
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
                      cudaStream_t s, const Tune &tn = Tune{});
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s);
