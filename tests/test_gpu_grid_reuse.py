@@ -118,3 +118,31 @@ def test_every_path_between_predicts_leaves_the_next_one_correct():
     predict_pair()
     enc.sync_status()
     enc.close()
+
+
+def test_rows_left_by_earlier_slices_are_never_read():
+    # The pixel-sum grid is not cleared between calls after the bucket sort:
+    # rows of pixels without events keep whatever an earlier slice left.
+    # Slices with disjoint occupancy follow one another on one context, one
+    # of them with a bucket above its shared-memory stage (records placed
+    # straight into the bucket's region) and one that puts a pixel across
+    # many record ranges; each result is checked against the oracle.
+    mode = vk.MLP_FP16
+    dense = _sl(401, 40_000)
+    rng = np.random.default_rng(9)
+    m = 12_000  # the first 32 pixels of row 0: about 12,000 records in one bucket
+    hot = synth.EventSlice(rng.integers(0, 32, m).astype(np.int16), np.zeros(m, np.int16),
+                           np.sort(rng.integers(dense.t_ref, dense.t_ref + 20_000, m)).astype(np.uint32),
+                           np.ones(m, np.int8), W, H, dense.t_ref)
+    one = 3_000  # a single pixel across about 24 ranges of 128 records
+    single = synth.EventSlice(np.full(one, 77, np.int16), np.full(one, 50, np.int16),
+                              np.sort(rng.integers(dense.t_ref, dense.t_ref + 20_000, one)).astype(np.uint32),
+                              np.ones(one, np.int8), W, H, dense.t_ref)
+    enc, TXY, w = make(dense, D, mode=mode, t_span_us=20_000)
+    for sl in (dense, hot, dense, single, hot, _sl(402, 15_000)):
+        _check_predict(enc, sl, TXY, w, mode)
+        x, y, t = to_dev(sl)
+        emb = enc.encode(x, y, t, sl.t_ref).cpu().numpy()
+        assert emb_rel_err(emb, _emb_ref(sl, TXY)).max() <= EMB_TOL_FP32
+    enc.sync_status()
+    enc.close()
