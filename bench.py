@@ -1,8 +1,8 @@
 """Benchmark: normal flows per second of the encoder + flow head on one slice.
 
 One step = one veckm_predict over the whole slice (every event is a requested
-flow): clear, scatter, two pooling passes, window counts, gather fused with
-the perceptron.  Inputs are resident in HBM when the timed region starts; the
+flow): sort by pixel, per-pixel phase sums, two pooling passes, window counts,
+gather fused with the perceptron.  Inputs are resident in HBM when the timed region starts; the
 accumulators written by every step (2 x 157 MB at 640x480, D=64) exceed the
 129 MB L2, so no explicit flush is needed between steps.
 
@@ -46,8 +46,76 @@ def _peaks():
                 "source": "fallback"}
 
 
+class _NvmlPoller:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    library, loaded with ctypes; read-only queries) every millisecond from a
+    thread, so that a timed region of a few milliseconds still gets samples.
+    Reason bits are NVML's public clock-event reason flags."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, device: int):
+        import ctypes as C
+        self.C = C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        import torch
+        want = str(torch.cuda.get_device_properties(device).uuid).lower().replace("gpu-", "")
+        count = C.c_uint()
+        if lib.nvmlDeviceGetCount_v2(C.byref(count)) != 0:
+            raise RuntimeError("nvmlDeviceGetCount failed")
+        handles = []
+        for i in range(count.value):
+            h, buf = C.c_void_p(), C.create_string_buffer(96)
+            if lib.nvmlDeviceGetHandleByIndex_v2(i, C.byref(h)) != 0:
+                continue
+            if lib.nvmlDeviceGetUUID(h, buf, 96) != 0:
+                continue
+            handles.append((buf.value.decode("ascii").lower().replace("gpu-", ""), h))
+        match = [h for u, h in handles if u == want]
+        if not match and len(handles) == 1:
+            match = [handles[0][1]]
+        if not match:
+            raise RuntimeError("no NVML device with the CUDA device's UUID")
+        self.h = match[0]
+        self.lib = lib
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        mx = C.c_uint()
+        self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(self.h, 1, C.byref(mx)) == 0 \
+            else None
+        self.samples, self.flags = [], 0
+        self.run = False
+
+    def _loop(self):
+        C = self.C
+        mhz, rs = C.c_uint(), C.c_ulonglong()
+        while self.run:
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) == 0:  # 1: SM clock
+                self.samples.append(float(mhz.value))
+            if self.reasons_fn(self.h, C.byref(rs)) == 0:
+                self.flags |= int(rs.value)
+            time.sleep(0.001)
+
+    def start(self):
+        self.run = True
+        self.th = threading.Thread(target=self._loop, daemon=True)
+        self.th.start()
+
+    def stop(self):
+        self.run = False
+        self.th.join(timeout=2)
+        if not self.samples:
+            return None
+        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
+                "samples": len(self.samples), "source": "nvml, 1 ms polling",
+                "reasons": sorted(v for k, v in self.REASONS.items() if self.flags & k)}
+
+
 class ClockSampler:
-    """nvidia-smi clock and throttle samples while the timed region runs."""
+    """Clock and throttle samples while the timed region runs: NVML polled
+    in-process when the driver's library loads, else nvidia-smi."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -55,9 +123,17 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.nvml = None
         self.lines = []
 
     def start(self):
+        self.nvml = None
+        try:
+            self.nvml = _NvmlPoller(self.index)
+            self.nvml.start()
+            return
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
@@ -73,6 +149,11 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            r = self.nvml.stop()
+            if r is not None:
+                return r
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()

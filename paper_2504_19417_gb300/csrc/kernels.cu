@@ -579,23 +579,28 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_sort(const int4 *__r
     // rows of the pixels at range edges inside [base, base + nrec): one warp
     // per range, lanes over the row's units.  Their pixels are read back from
     // the slots just written (shared memory when staged, else this block's
-    // own global writes, visible after the barrier)
+    // own global writes, visible after the barrier).  A range's last pixel
+    // is skipped when the next range starts with it inside this bucket (it
+    // is zeroed as that range's first pixel).
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t c0 = base / kPixRecs, c1 = ((int64_t)base + nrec - 1) / kPixRecs;
+    const int64_t end = (int64_t)base + nrec;
+    auto pixel_at = [&](int64_t pos) -> int {
+      if (staged) {
+        const int r = src[pos - base];
+        return r >= 0 && r < nrec ? st_p[r] : -1;
+      }
+      return rpix[pos];
+    };
+    const int64_t c0 = base / kPixRecs, c1 = (end - 1) / kPixRecs;
     for (int64_t c = c0 + warp; c <= c1; c += blockDim.x >> 5) {
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int64_t pos = c * kPixRecs + (e ? kPixRecs - 1 : 0);
-        if (pos < base || pos >= (int64_t)base + nrec) continue;
-        int p = -1;
-        if (staged) {
-          const int r = src[pos - base];
-          if (r >= 0 && r < nrec) p = st_p[r];
-        } else {
-          p = rpix[pos];
-        }
+        if (pos < base || pos >= end) continue;
+        const int p = pixel_at(pos);
         if (p < p0 || p - p0 >= width || p >= P) continue;
+        if (e && pos + 1 < end && pixel_at(pos + 1) == p) continue;
         for (int u = lane; u < zunits; u += 32) zgrid[(size_t)p * zunits + u] = f4zero();
       }
     }
