@@ -189,10 +189,12 @@ const char *veckm_last_error(void);
 veckm_status veckm_get_frequencies(const veckm_ctx *ctx, double *h_T, double *h_X, double *h_Y);
 
 /* Per-stage timing, measured with CUDA events recorded on the launching
- * stream around each stage.  Stages: 0 clear (memset of the accumulators),
+ * stream around each stage.  Stages: 0 sort of the events by pixel (and, where
+ * the pixel sums need a cleared grid, the wait for its clear on a side stream),
  * 1 per-pixel accumulation (the first loop of Algorithm 1), 2 pooling row pass,
- * 3 window counts (Eq. 17), 4 pooling column pass (the window sums of
- * Eq. 16), 5 gather + normalise, fused with the perceptron in veckm_predict.
+ * 3 window counts (Eq. 17; they run on a side stream, so this is the residual
+ * wait for them), 4 pooling column pass (the window sums of Eq. 16), 5 gather
+ * + normalise, fused with the perceptron in veckm_predict.
  * veckm_stage_times synchronises, writes the elapsed milliseconds summed over
  * every timed call since the last read into ms[0..nstage-1] and the number of
  * timed calls into calls[0..nstage-1] (may be NULL), then resets. */
@@ -207,8 +209,8 @@ int veckm_last_launch_count(const veckm_ctx *ctx);
  * per flow in Eq. runtime of Section 2.2.2).  The dense form pools every
  * pixel once with separable box sums (cost per pixel, then little per flow);
  * the direct form keeps the window loop, visiting only occupied window pixels
- * (one warp per requested event), and skips the pooling passes and the clear
- * of the pixel grid.  VECKM_PATH_AUTO (default) picks per call the smaller of
+ * (one warp per requested event), and skips the pooling passes.
+ * VECKM_PATH_AUTO (default) picks per call the smaller of
  *   dense:  k_pixel * W*H + k_flow_dense * nK
  *   direct: k_flow_window * (2dx+1)(2dy+1) * nK,
  * with coefficients measured on GB300 (settable).  The direct form's
