@@ -45,6 +45,7 @@ CASES = [
     (64, 40, 2_500, 20_000, 64, 3, 7, 16_000),         # dx != dy
     (45, 33, 1_500, 5_000, 192, 0, 2, 16_000),         # dx = 0, D=192
     (15, 9, 600, 10_000, 256, 10, 10, 16_000),         # sensor smaller than the window, D=256
+    (120, 90, 5_000, 20_000, 64, 20, 18, 16_000),      # window wider than 32: a cleared sum grid
 ]
 
 
@@ -97,6 +98,21 @@ def test_predict_matches_oracle(mode, W, H, n, D):
     flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
     enc.sync_status()
     _check_flow(flow, _oracle_emb(sl, D, 10, 10, 16_000, TXY), w, mode)
+
+
+def test_wide_window_predicts_alternate_cleared_grids():
+    # 41 x 37 windows: the row pass reads every pixel, so the pixel sums go
+    # to a grid cleared for them (by the previous call's head, else on the
+    # side stream); dense and sparse slices alternate on one context
+    mode, D, dx, dy = vk.MLP_FP16, 64, 20, 18
+    sls = [synth.event_slice(120, 90, n, 10_000, n_edges=5, seed=600 + i)
+           for i, n in enumerate((9_000, 1_500, 9_000, 700))]
+    enc, TXY, w = make(sls[0], D, dx, dy, mode=mode, t_span_us=10_000)
+    for sl in sls:
+        x, y, t = to_dev(sl)
+        flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+        _check_flow(flow, _oracle_emb(sl, D, dx, dy, 16_000, TXY), w, mode)
+    enc.sync_status()
 
 
 def test_switching_precision_keeps_encoder_state():
