@@ -182,6 +182,25 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def _oracle_single_thread(oracle, sl, D, T, X, Y, w, K):
+    """The same oracle call on one host thread (a smaller sample), beside the
+    all-core figure; None if it cannot be timed."""
+    cores = oracle.num_threads()
+    try:
+        oracle.set_num_threads(1)
+        t0 = time.perf_counter()
+        emb, _ = oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D,
+                                      10, 10, 16_000.0, T, X, Y, K=K)
+        oracle.mlp(emb, w.W1, w.b1, w.W2, w.b2)
+        dt = time.perf_counter() - t0
+        return {"value": len(K) / dt, "unit": UNIT, "cores": 1,
+                "sample": f"{len(K)} of the same requested events, {dt:.1f} s"}
+    except Exception:
+        return None
+    finally:
+        oracle.set_num_threads(cores)
+
+
 def _kernel_traffic(name: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
     source is unchanged since the capture (source hash recorded beside it)."""
@@ -504,6 +523,9 @@ def run_ours(args):
             "value": S / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{S} random requested events of the {sl.n}-event slice (all events "
                       f"scattered), FP64 pooled form + perceptron, {dt:.1f} s"}
+        single = _oracle_single_thread(oracle, sl, D, T, X, Y, w, K[: max(1, S // 10)])
+        if single:
+            out["cpu_baseline"]["single_thread"] = single
         Kd = torch.from_numpy(K).cuda()
         emb_g = enc.encode(x, y, t, sl.t_ref, K=Kd).cpu().numpy().astype(np.float64)
         flow_g = enc.predict(x, y, t, sl.t_ref, K=Kd).cpu().numpy().astype(np.float64)
