@@ -115,18 +115,24 @@ veckm_status veckm_encode(veckm_ctx *ctx, const int16_t *d_x, const int16_t *d_y
                           const int64_t *d_K, int64_t nK, float *d_emb, void *stream);
 
 /* Encode without allocating: the same result as veckm_encode, for callers
- * that may not allocate device memory during a call (graph recording,
- * real-time loops, devices whose memory is reserved up front).  veckm_encode
- * may grow its per-event buffers with cudaMalloc; this call takes them from a
- * fixed array in device memory that the library declares statically and
- * never calls cudaMalloc, cudaFree or any allocating routine.  The paper has
- * no counterpart; it is a deployment variant.
+ * that may not allocate device memory during a call.  A loop with a real-time
+ * budget cannot wait for an allocation and the synchronisation before it; a
+ * process that reserves all of a device's memory up front for its own
+ * allocator finds cudaMalloc failing.  veckm_encode may grow its per-event
+ * buffers with cudaMalloc; this call takes them from a fixed array in device
+ * memory that the library declares statically and never calls cudaMalloc,
+ * cudaFree or any allocating routine.  The paper has no counterpart; it is a
+ * deployment variant.
  *   - At most 1048576 events per call (n); larger n returns VECKM_EINVAL.
  *   - The array (12 MiB) exists on every GPU that loads the library until the
  *     process exits.  The first call on a device looks up its address there
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for that device's CUDA context; make
+ *     that first call before any stream capture.  After a device reset the
+ *     next call looks the address up again.
  *   - All calls on a device share the array and the context's accumulators:
  *     calls that may overlap on the GPU race and must be serialised.
+ *   - It always uses the histogram-and-placement sort and clears the
+ *     per-pixel sums in full, so it runs slower than veckm_encode.
  * Arguments, layout and errors are those of veckm_encode. */
 veckm_status veckm_encode_noalloc(veckm_ctx *ctx, const int16_t *d_x, const int16_t *d_y,
                                   const uint32_t *d_t, int64_t n, uint32_t t_ref_us,
@@ -336,13 +342,16 @@ veckm_status veckm_stream_create(veckm_ctx *ctx, int64_t window_us, int64_t capa
                                  veckm_stream **out);
 /* Push a packet of n events (device x, y int16; t uint32 microseconds, the
  * stream's absolute times, sorted, all >= the previous packet's) that ends
- * at t_hi_us.  The window becomes [t_hi_us - window_us, t_hi_us]; the
- * packet's events are encoded against it (predict == 0: d_out float
- * [n][2D] encodings; else d_out float [n][2] flows).  An event outside the
- * sensor or the window, or out of time order, is not added and its output
- * row is zeroed (VECKM_ERANGE at the next status check); events beyond the
- * ring's capacity likewise (VECKM_EBUSY).  Never synchronises.  n may be 0
- * (the window still slides to t_hi_us). */
+ * at t_hi_us, which may not be earlier than the previous push's (else
+ * VECKM_EINVAL, nothing enqueued).  The window becomes [t_hi_us - window_us,
+ * t_hi_us]; the packet's events are encoded against it (predict == 0: d_out
+ * float [n][2D] encodings; else d_out float [n][2] flows).  An event outside
+ * the sensor or the window is not added, nor one earlier than an event
+ * accepted before it (in an earlier packet, or earlier in this one inside
+ * the sensor and the window), so the window's events stay in time order;
+ * such an event's output row is zeroed (VECKM_ERANGE at the next status
+ * check); events beyond the ring's capacity likewise (VECKM_EBUSY).  Never
+ * synchronises.  n may be 0 (the window still slides to t_hi_us). */
 veckm_status veckm_stream_push(veckm_stream *st, const int16_t *d_x, const int16_t *d_y,
                                const uint32_t *d_t, int64_t n, uint32_t t_hi_us, float *d_out,
                                int32_t predict, void *stream);

@@ -26,6 +26,7 @@ struct veckm_ctx {
   uint2 *wxy = nullptr;  // X then Y frequencies in 64-bit fixed-point turns per pixel
   float *W1 = nullptr, *W1t = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
   uint16_t *W1h = nullptr;
+  uint16_t *W2h = nullptr;  // second layer of the tensor-core head (FP16, 16 x hidden)
   float4 *acc = nullptr, *hbuf = nullptr;
   // Which of the two grids (0: acc, 1: hbuf; -1: neither) is known to hold
   // zeros over its first zero_units float4, in stream order: the tensor-core
@@ -100,7 +101,7 @@ struct veckm_ctx {
   }
   veckm::MLP mlp() const {
     return veckm::MLP{W1,     W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0,
-                      hb1.data(), hW2.data(), hb2.data()};
+                      hb1.data(), hW2.data(), hb2.data(), W2h};
   }
 };
 

@@ -705,19 +705,25 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
 // same phase, advancing in y from an anchor per output block.
 enum class Pass { Rows, Cols };
 
-// HALF (column pass only): the output is divided by the pixel's window count
-// n (Eq. 17; 0 where the window is empty) and stored as FP16, unit u of a
-// pixel = 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
+// EMIT (column pass only) picks the output form: kEmitF32, the window sums
+// as they are; kEmitF16N, divided by the pixel's window count n (Eq. 17; 0
+// where the window is empty) and stored as FP16, unit u of a pixel = 8 bytes
+// (Re 2u, Re 2u+1, Im 2u, Im 2u+1); kEmitF32N, divided by n and stored as
+// FP32 in the order (Re 2u, Re 2u+1, Im 2u, Im 2u+1), so that the real and the
+// imaginary parts of a unit are register pairs for packed FP32x2 arithmetic.
 // occ (row pass, window length L <= 32): per-pixel event counts; pixels with
 // none are taken as zero without reading src, whose rows there may hold
 // anything.
-template <int DV, Pass P, bool HALF = false>
+enum : int { kEmitF32 = 0, kEmitF16N = 1, kEmitF32N = 2 };
+template <int DV, Pass P, int EMIT = kEmitF32>
 __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
                                                  int seg, int nseg, int up,
                                                  const int *__restrict__ ncnt = nullptr,
                                                  const int *__restrict__ occ = nullptr) {
-  static_assert(!HALF || P == Pass::Cols, "FP16 output is written by the column pass");
+  static_assert(EMIT == kEmitF32 || P == Pass::Cols, "normalised output: column pass only");
+  constexpr bool HALF = EMIT == kEmitF16N;
+  constexpr bool NORM = EMIT != kEmitF32;  // divided by the window counts
   constexpr int U = 32 * DV;
   extern __shared__ float4 smem[];
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
@@ -825,14 +831,14 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     }
   };
 
-  // HALF: window counts of output block bb, one per lane (the reciprocal is
+  // NORM: window counts of output block bb, one per lane (the reciprocal is
   // taken where they are used, a block later, so the load is not waited on)
   auto load_cnt = [&](int bb) {
     const int q = lane < L ? lane : 0;
     const int j = bb * L + q;
     return j < nout ? __ldg(ncnt + (size_t)(o0 + j) * g.W + line) : 0;
   };
-  int cnt_next = HALF ? load_cnt(0) : 0;
+  int cnt_next = NORM ? load_cnt(0) : 0;
 
   issue(0);
   issue(1);
@@ -851,15 +857,15 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
 #pragma unroll
       for (int v = 0; v < DV; ++v) dph[v] = cmul2(fl[v], S[L * U + lane + 32 * v]);
     }
-    float inv_lane = 0.f;  // HALF: 1/n of output j0 + lane (lanes < L), loaded a block ahead
-    if (HALF) {
+    float inv_lane = 0.f;  // NORM: 1/n of output j0 + lane (lanes < L), loaded a block ahead
+    if (NORM) {
       inv_lane = cnt_next > 0 ? 1.0f / (float)cnt_next : 0.f;
       if (b + 1 < nb) cnt_next = load_cnt(b + 1);
     }
     auto emit = [&](int j, int qs, const float4 *G) {
       const int pos = o0 + j;
       float inv = 0.f;
-      if (HALF) inv = __shfl_sync(kFull, inv_lane, j - j0);
+      if (NORM) inv = __shfl_sync(kFull, inv_lane, j - j0);
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
         const int u = lane + 32 * v;
@@ -875,6 +881,9 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
           reinterpret_cast<uint2 *>(dst)[base + (size_t)pos * stride + u] =
               make_uint2(*reinterpret_cast<const uint32_t *>(&re),
                          *reinterpret_cast<const uint32_t *>(&im));
+        } else if (EMIT == kEmitF32N) {
+          dst[base + (size_t)pos * stride + u] =
+              make_float4(o.x * inv, o.z * inv, o.y * inv, o.w * inv);
         } else {
           dst[base + (size_t)pos * stride + u] = o;
         }
@@ -1375,7 +1384,7 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
 // Largest dynamic shared memory a box-pass block may ask for.
 constexpr size_t kBoxSmemMax = 200 * 1024;
 
-template <int DV, Pass P, bool HALF = false>
+template <int DV, Pass P, int EMIT = kEmitF32>
 int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s,
              const int *ncnt, int seg_windows, int wpb_req, const int *occ = nullptr) {
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
@@ -1391,10 +1400,10 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
   if (wpb_req > 0 && wpb_req <= 4 && per_warp * wpb_req <= kBoxSmemMax) wpb = wpb_req;
   const size_t sm = per_warp * wpb;
-  if (set_smem(k_box_pass<1, P, HALF>, sm) != cudaSuccess) return -1;
+  if (set_smem(k_box_pass<1, P, EMIT>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const dim3 grid((unsigned)((warps + wpb - 1) / wpb), DV);
-  k_box_pass<1, P, HALF><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, 32 * DV, ncnt,
+  k_box_pass<1, P, EMIT><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, 32 * DV, ncnt,
                                                     occ);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -1613,9 +1622,15 @@ int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, fl
 
 int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbuf,
                           const int *ncnt, void *pooled16, cudaStream_t s, const Tune &tn) {
-  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, true>(g, tb, hbuf,
-                                                         reinterpret_cast<float4 *>(pooled16), s,
-                                                         ncnt, tn.cols_seg, tn.cols_wpb)));
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, kEmitF16N>(g, tb, hbuf,
+                                                              reinterpret_cast<float4 *>(pooled16),
+                                                              s, ncnt, tn.cols_seg, tn.cols_wpb)));
+}
+
+int launch_pool_cols_norm(const Geometry &g, const Tables &tb, const float4 *hbuf,
+                          const int *ncnt, float4 *pooled, cudaStream_t s, const Tune &tn) {
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, kEmitF32N>(g, tb, hbuf, pooled, s, ncnt,
+                                                              tn.cols_seg, tn.cols_wpb)));
 }
 
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s) {

@@ -21,20 +21,26 @@
 //     the accumulator back with tcgen05.ld (warp w owns TMEM lanes
 //     32w..32w+31, one event row per thread), applies the window count
 //     normalisation and b1 in one FMA (the first layer is linear, so
-//     W1 (x / n) = (W1 x) / n), ReLU, and contracts with the 2 x 128 second
-//     layer on the CUDA cores.
+//     W1 (x / n) = (W1 x) / n), and writes ReLU(h) as FP16 pairs back into
+//     the first 64 columns of the same accumulator (tcgen05.st).  The second
+//     layer then runs on the tensor cores too: one 128 x 16 x 128 MMA chain
+//     (K steps of 16) with A = ReLU(h) read from tensor memory and B = W2
+//     (2 x 128, padded to 16 rows, FP16 in shared memory) writes the two
+//     outputs into columns 64..79 of the accumulator, which the epilogue
+//     reads back (tcgen05.ld), adds b2 to, and stores.
 // Shared tiles and accumulators are double buffered; the hand-offs are
 // mbarriers (full: producers -> epilogue/MMA; mma_done: MMA -> epilogue;
-// tmem_empty: epilogue -> MMA and producers).  No waiter can fall two phases
-// behind a barrier (each role's next use of a buffer waits for the other
-// roles' previous use), so parity waits are unambiguous.  Every wait is
+// stored: epilogue -> second-layer MMA; out_done: second-layer MMA ->
+// epilogue; tmem_empty: epilogue -> MMA and producers).  No waiter can fall
+// two phases behind a barrier (each role's next use of a buffer waits for the
+// other roles' previous use), so parity waits are unambiguous.  Every wait is
 // bounded: on time-out the kernel sets the error word and leaves.
 //
 // While they wait for accumulators, the epilogue warps can also zero a grid
 // buffer for the caller (the next call's per-pixel sums): each CTA clears one
 // contiguous share, a slice per tile, and on an early exit the rest of it.
 //
-// b1, W2 and b2 reach the epilogue as a kernel parameter: read through the
+// b1 and b2 reach the epilogue as a kernel parameter: read through the
 // constant cache, they take no slots of the shared-memory pipe, which the
 // producers' loads and tile stores and the MMAs' operand reads share.
 //
@@ -70,11 +76,16 @@ struct Shape {
 };
 constexpr int kMmaWarp = 0;  // epilogue warp 0 also issues the MMAs
 constexpr int kTmemCols = 2 * kN;  // two accumulators
+// Second layer: N = 16 (the two outputs, padded), K = kN.  Its A operand,
+// ReLU(h) as FP16 pairs, takes accumulator columns [0, kN/2); its outputs
+// land in columns [kOutCol, kOutCol + 16) of the same accumulator.
+constexpr int kN2 = 16;
+constexpr int kOutCol = kN / 2;
+constexpr int kW2Bytes = kN2 * kN * 2;  // W2 as FP16, K-major, 128-byte swizzled
 
-// Second-layer weights and first-layer bias, by value.
+// First-layer bias and second-layer bias, by value.
 struct __align__(16) EpiParams {
   float b1[kN];
-  float w2[2][kN];
   float b2[2];
 };
 // Output row codes (event counts are below 2^30): k >= 0 writes the flow of
@@ -85,11 +96,6 @@ constexpr long long kWaitLimitCycles = 4000000000LL;  // ~2 s at 2 GHz, then giv
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ float4 cmul2c(float4 a, float4 b) {
-  return make_float4(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y),
-                     fmaf(a.z, b.z, a.w * b.w), fmaf(a.w, b.z, -a.z * b.w));
 }
 
 // Shared-memory matrix descriptor, K-major with 128-byte swizzling: start
@@ -141,6 +147,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// a * b and a - b on two FP32 lanes at once (packed FP32x2, one instruction)
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const uint64_t *>(&a)), "l"(*reinterpret_cast<const uint64_t *>(&b)));
+  return *reinterpret_cast<const float2 *>(&d);
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const uint64_t *>(&a)), "l"(*reinterpret_cast<const uint64_t *>(&b)));
+  return *reinterpret_cast<const float2 *>(&d);
+}
+
 // d = a * b + c on two FP32 lanes at once (packed FP32x2, one instruction)
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   uint64_t d;
@@ -155,18 +177,40 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 32 consecutive FP32 accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive 32-bit accumulator columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+
+// ReLU(lo), ReLU(hi) rounded to FP16 and packed (lo in the low half).
+__device__ __forceinline__ uint32_t relu_f16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 // Loads N consecutive ints of shared memory (16-byte aligned for N >= 4,
@@ -204,29 +248,38 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;                            // 2 x [128 x IN] half, SW128
   uint8_t *sB = smem + 2 * TILE_BYTES;           // [128 x IN] half (W1), SW128
-  float *sInv = reinterpret_cast<float *>(sB + TILE_BYTES);   // [2][128] 1 / window count
+  uint8_t *sW2 = sB + TILE_BYTES;                // [16 x 128] FP16 (W2 padded), SW128
+  float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);    // [2][128] 1 / window count
   int *sK = reinterpret_cast<int *>(sInv + 2 * kM);            // [2][128] output row codes
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 2 * kM);  // full[2], done[2], empty[2]
-  int *sMeta = reinterpret_cast<int *>(bars + 6);  // per producer warp [2][pixels R | t R]
+  // full[2], done[2], empty[2], stored[2], out_done[2]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 2 * kM);
+  int *sMeta = reinterpret_cast<int *>(bars + 10);  // per producer warp [2][pixels R | t R]
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sMeta + kProdWarps * 4 * kRowsPerWarp);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int fp16 = F16 ? 1 : 0;
 
-  {  // W1 (already in SW128 order)
+  {  // W1 and W2 (already in SW128 order)
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
     uint4 *dst = reinterpret_cast<uint4 *>(sB);
     for (int i = tid; i < TILE_BYTES / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    const uint4 *src2 = reinterpret_cast<const uint4 *>(mlp.W2h);
+    uint4 *dst2 = reinterpret_cast<uint4 *>(sW2);
+    for (int i = tid; i < kW2Bytes / 16; i += blockDim.x) dst2[i] = __ldg(src2 + i);
   }
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int b) { return bar0 + 8u * b; };
   auto done_bar = [&](int b) { return bar0 + 8u * (2 + b); };
   auto empty_bar = [&](int b) { return bar0 + 8u * (4 + b); };
+  auto stored_bar = [&](int b) { return bar0 + 8u * (6 + b); };
+  auto out_bar = [&](int b) { return bar0 + 8u * (8 + b); };
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full_bar(b)), "r"(kProdWarps));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_bar(b)));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty_bar(b)), "r"(kEpiWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(stored_bar(b)), "r"(kEpiWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(out_bar(b)));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -276,12 +329,12 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
               (u & 1) * 8;
     }
     // Row metadata of tile t for lane j < 16 (row pw*16 + j): the pixel whose
-    // pooled vector is read, t - t_ref, 1 for a valid event (0 otherwise; the
-    // FP32-grid path later replaces it by 1/n) and the output row (-1: none;
-    // invalid_row(i): an invalid event whose flow is written as zeros).  Rows
-    // past the end and invalid events read pixel 0: the MMA keeps rows apart
-    // and their results are discarded.  Every load here is consumed a tile
-    // later, so the warp never waits on it.
+    // pooled vector is read, t - t_ref, 1 for a valid event (0 otherwise;
+    // the pooled grid is already divided by the window counts) and the output
+    // row (-1: none; invalid_row(i): an invalid event whose flow is written as
+    // zeros).  Rows past the end and invalid events read pixel 0: the MMA
+    // keeps rows apart and their results are discarded.  Every load here is
+    // consumed a tile later, so the warp never waits on it.
     auto meta = [&](int t, int &pix, uint32_t &trel, float &inv, int &outk) {
       const int i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
       pix = 0;
@@ -329,8 +382,9 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       }
     };
     const uint32_t sA_a = smem_u32(sA);
-    // FP16 grid: uint2 (half2 Re pair, half2 Im pair) per unit, already
-    // divided by n; FP32 grid: float4 (re 2u, im 2u, re 2u+1, im 2u+1)
+    // both grids are already divided by n; FP16 grid: uint2 (half2 Re pair,
+    // half2 Im pair) per unit; FP32 grid: float4 (re 2u, re 2u+1, im 2u,
+    // im 2u+1), the real and imaginary pairs of packed FP32x2 arithmetic
     using Q = typename std::conditional<HALF, uint2, float4>::type;
     const Q *pooled = reinterpret_cast<const Q *>(pooled_v);
     // rows per batch: the loads of one batch are in flight while the previous
@@ -367,7 +421,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
           // (c0, s0, c1, s1); the lean form needs a register the FP16 grid's
           // variant has no room for
           const float4 ph = HALF ? time_phase2(tj, wf[v][0], wf[v][1])
-                                 : time_phase2_lean(tj, wf[v][0], wf[v][1]);
+                                 : time_phase2_packed(tj, wf[v][0], wf[v][1]);
           uint32_t wre, wim;
           if constexpr (HALF) {
             // P conj(phase) in packed half2: Re = PR c + PI s, Im = PI c - PR s
@@ -386,9 +440,16 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
               wim = pack2(fi.x, fi.y, 0);
             }
           } else {
-            const float4 e = cmul2c(q[r][v], ph);
-            wre = pack2(e.x, e.z, fp16);
-            wim = pack2(e.y, e.w, fp16);
+            // P conj(phase) on the pairs R = (Re 2u, Re 2u+1), I = (Im 2u,
+            // Im 2u+1), C = (c0, c1), S = (s0, s1): Re = R C + I S,
+            // Im = I C - R S, each pair in one packed FP32x2 instruction
+            const float2 R = make_float2(q[r][v].x, q[r][v].y);
+            const float2 I = make_float2(q[r][v].z, q[r][v].w);
+            const float2 C = make_float2(ph.x, ph.z), S = make_float2(ph.y, ph.w);
+            const float2 er = ffma2(R, C, fmul2(I, S));
+            const float2 ei = fsub2(fmul2(I, C), fmul2(R, S));
+            wre = pack2(er.x, er.y, fp16);
+            wim = pack2(ei.x, ei.y, fp16);
           }
           *reinterpret_cast<uint2 *>(Ag + ((lo[v] ^ (uint32_t)((j & 7) * 0x90)) + (j >> 3) * 1024)) =
               make_uint2(wre, wim);
@@ -397,7 +458,6 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     };
     int c_outk = -1;
     float c_inv = 0.f;
-    int n_cnt = 0;  // FP32 grid: window count of this lane's row in the next tile
     // pixels of this lane's row in the tile two ahead of the current one,
     // whose pooled rows are prefetched into L2 (sorted path only)
     int pf_pix = -1;
@@ -409,7 +469,6 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       int pix;
       uint32_t trel;
       meta(blockIdx.x, pix, trel, c_inv, c_outk);
-      if (!HALF && c_inv != 0.f) c_inv = 1.0f / (float)__ldg(ncnt + pix);
       ms_put(0, pix, trel);
       __syncwarp();
       issue(0, 0, qa);
@@ -451,9 +510,6 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         }
         if (h & 1) compute(b, h * kB, qb, Abuf);
         else compute(b, h * kB, qa, Abuf);
-        // FP32 grid: the window count of the next tile's row, loaded mid-tile
-        // (its pixel has arrived by then) and inverted at the tile's end
-        if (!HALF && h == NB / 2 - 1 && has_next && n_inv != 0.f) n_cnt = __ldg(ncnt + n_pix);
       }
       // the epilogue reads these after the full barrier
       if (lane < kRowsPerWarp) {
@@ -464,7 +520,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(full_bar(b));
       c_outk = n_outk;
-      c_inv = (!HALF && n_inv != 0.f) ? 1.0f / (float)n_cnt : n_inv;
+      c_inv = n_inv;
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -474,7 +530,9 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     constexpr uint32_t idesc_bf16 = make_idesc(0, kM, kN);
     constexpr uint32_t idesc_fp16 = make_idesc(1, kM, kN);
     const uint32_t idesc = fp16 ? idesc_fp16 : idesc_bf16;
-    const uint32_t sA_a = smem_u32(sA), sB_a = smem_u32(sB);
+    constexpr uint32_t idesc2 = make_idesc(1, kM, kN2);  // second layer: FP16 x FP16
+    const uint32_t sA_a = smem_u32(sA), sB_a = smem_u32(sB), sW2_a = smem_u32(sW2);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     // this CTA's share [z0, z1) of the buffer to zero, one slice per tile
     int64_t z0 = 0, z1 = 0, zstep = 0;
     if (zero_buf) {
@@ -490,14 +548,15 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     int zeroed = 0;  // slices this thread has cleared
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
+      const uint32_t par = (li >> 1) & 1;
       // full: the producers' tile and row metadata
-      if (!mbar_wait(full_bar(b), (li >> 1) & 1)) {
+      if (!mbar_wait(full_bar(b), par)) {
         ok = false;
         break;
       }
       if (warp == kMmaWarp) {
         // accumulator b is free once all epilogue warps have read tile li - 2
-        if (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1)) {
+        if (li >= 2 && !mbar_wait(empty_bar(b), par ^ 1)) {
           ok = false;
           break;
         }
@@ -525,43 +584,82 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         }
         __syncwarp();
       }
-      // done: the accumulator
-      if (!mbar_wait(done_bar(b), (li >> 1) & 1)) {
+      // done: the first layer's accumulator
+      if (!mbar_wait(done_bar(b), par)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float inv = sInv[b * kM + row];
       const int k = sK[b * kM + row];
-      // packed FP32x2 arithmetic: even and odd columns in the two halves
-      float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
       const float2 inv2 = make_float2(inv, inv);
-      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kN);
+      const uint32_t acc_t = tmem + lane_base + (uint32_t)(b * kN);
+      // ReLU(h / n + b1) as FP16 pairs into columns [0, kN/2): chunk c reads
+      // columns [32c, 32c + 32) and writes [16c, 16c + 16), which earlier
+      // chunks (or this one) have already read
 #pragma unroll
-      for (int c0 = 0; c0 < kN; c0 += 16) {
-        float h[16];
-        tmem_ld16(base + c0, h);
+      for (int c0 = 0; c0 < kN; c0 += 32) {
+        float h[32];
+        tmem_ld32(acc_t + c0, h);
+        uint32_t pk[16];
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) {
+        for (int j = 0; j < 32; j += 4) {
           const float4 bb = *reinterpret_cast<const float4 *>(ep.b1 + c0 + j);
-          const float4 w0 = *reinterpret_cast<const float4 *>(ep.w2[0] + c0 + j);
-          const float4 w1 = *reinterpret_cast<const float4 *>(ep.w2[1] + c0 + j);
-          float2 a01 = ffma2(make_float2(h[j], h[j + 1]), inv2, make_float2(bb.x, bb.y));
-          float2 a23 = ffma2(make_float2(h[j + 2], h[j + 3]), inv2, make_float2(bb.z, bb.w));
-          a01.x = fmaxf(a01.x, 0.f); a01.y = fmaxf(a01.y, 0.f);
-          a23.x = fmaxf(a23.x, 0.f); a23.y = fmaxf(a23.y, 0.f);
-          o0 = ffma2(a01, make_float2(w0.x, w0.y), o0);
-          o0 = ffma2(a23, make_float2(w0.z, w0.w), o0);
-          o1 = ffma2(a01, make_float2(w1.x, w1.y), o1);
-          o1 = ffma2(a23, make_float2(w1.z, w1.w), o1);
+          const float2 a01 = ffma2(make_float2(h[j], h[j + 1]), inv2, make_float2(bb.x, bb.y));
+          const float2 a23 = ffma2(make_float2(h[j + 2], h[j + 3]), inv2, make_float2(bb.z, bb.w));
+          pk[j / 2] = relu_f16x2(a01.x, a01.y);
+          pk[j / 2 + 1] = relu_f16x2(a23.x, a23.y);
         }
+        tmem_st16(acc_t + c0 / 2, pk);
       }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(stored_bar(b));
+      if (warp == kMmaWarp) {
+        // the second layer once every epilogue warp has stored its rows
+        if (!mbar_wait(stored_bar(b), par)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (lane == 0) {
+          const uint32_t a_t = tmem + (uint32_t)(b * kN);
+          const uint32_t d_t = a_t + kOutCol;
+#pragma unroll
+          for (int kk = 0; kk < kN / 16; ++kk) {
+            // K-step kk: 8 columns of FP16 pairs; W2's K-block kk / 4, 32-byte step kk % 4
+            const uint64_t bd = make_desc_sw128(sW2_a + (kk >> 2) * (kN2 * 128) + (kk & 3) * 32);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_t),
+                "r"(a_t + (uint32_t)(kk * 8)), "l"(bd), "r"(idesc2), "r"(acc)
+                : "memory");
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  out_bar(b))
+              : "memory");
+        }
+        __syncwarp();
+      }
+      if (!mbar_wait(out_bar(b), par)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t r0, r1;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                   : "=r"(r0), "=r"(r1)
+                   : "r"(acc_t + kOutCol));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(empty_bar(b));
       if (k >= 0) {
         *reinterpret_cast<float2 *>(flow + 2 * (size_t)k) =
-            make_float2(o0.x + o0.y + b20, o1.x + o1.y + b21);
+            make_float2(__uint_as_float(r0) + b20, __uint_as_float(r1) + b21);
       } else if (k <= -2) {
         *reinterpret_cast<float2 *>(flow + 2 * (size_t)(-2 - k)) = make_float2(0.f, 0.f);
       }
@@ -578,7 +676,10 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
       // let MMAs that may still be in flight land before their TMEM is freed
-      for (int b = 0; b < 2; ++b) mbar_wait(done_bar(b), 0), mbar_wait(done_bar(b), 1);
+      for (int b = 0; b < 2; ++b) {
+        mbar_wait(done_bar(b), 0), mbar_wait(done_bar(b), 1);
+        mbar_wait(out_bar(b), 0), mbar_wait(out_bar(b), 1);
+      }
     }
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols));
@@ -594,8 +695,8 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
-  const size_t sm = (size_t)3 * kM * IN * 2 + sizeof(float) * (2 * kM) +
-                    sizeof(int) * 2 * kM + 8 * 6 + sizeof(int2) * 2 * kM +
+  const size_t sm = (size_t)3 * kM * IN * 2 + kW2Bytes + sizeof(float) * (2 * kM) +
+                    sizeof(int) * 2 * kM + 8 * 10 + sizeof(int2) * 2 * kM +
                     16 + 1024;  // + SW128 alignment slack
   auto kern = k_predict_tc<DV, HALF, F16>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
@@ -616,8 +717,6 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
                     (zero_units + grid - 1) / grid <= min_local * kZeroPerTile;
   EpiParams ep;
   std::copy(mlp.hb1, mlp.hb1 + kN, ep.b1);
-  std::copy(mlp.hW2, mlp.hW2 + kN, ep.w2[0]);
-  std::copy(mlp.hW2 + kN, mlp.hW2 + 2 * kN, ep.w2[1]);
   ep.b2[0] = mlp.hb2[0];
   ep.b2[1] = mlp.hb2[1];
   kern<<<grid, kThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,

@@ -3,18 +3,27 @@
 //
 // veckm_encode keeps its pixel-sorted event records in context buffers that
 // grow (cudaMalloc, after a stream synchronisation) whenever a call brings
-// more events than any call before.  Code that records CUDA graphs, runs
-// under a real-time budget, or shares a device whose memory is fully
-// reserved up front cannot allow that.  This entry point instead takes the
-// per-event records from one fixed array in device memory that the library
-// declares at file scope, so a call never allocates: it only launches
-// kernels and clears context buffers with cudaMemsetAsync.
+// more events than any call before.  Some callers cannot allow that: a loop
+// with a real-time budget (an allocation and the synchronisation before it
+// take an unbounded time), or a process that reserves all of a device's
+// memory up front for its own allocator, after which cudaMalloc fails.  This
+// entry point instead takes the per-event records from one fixed array in
+// device memory that the library declares at file scope, so a call never
+// allocates: it only launches kernels and clears context buffers with
+// cudaMemsetAsync.
 //
 // The array holds up to kNoAllocMaxEvents events (12 bytes each, 12 MiB in
 // all); every GPU that loads the library keeps it for the life of the
 // process.  All calls, from every context on a device, share it: calls that
 // may overlap on the GPU (two streams, two host threads) race on it and
 // must be serialised by the caller.
+//
+// The array's device address is looked up with cudaGetSymbolAddress by the
+// first call on a device (with that device current) and kept per device,
+// together with the identity of the CUDA context it belongs to; a device
+// reset (cudaDeviceReset) ends that context, and the next call looks the
+// address up again.  The first call on a device should therefore come before
+// any stream capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -32,18 +41,52 @@ static __device__ __align__(256) unsigned char g_noalloc_records[kRecordBytes];
 
 constexpr int kMaxDevices = 256;
 std::mutex g_mutex;
-void *g_records_addr[kMaxDevices] = {};  // device address of g_noalloc_records, per device
+// per device: the device address of g_noalloc_records and the id of the CUDA
+// context it was looked up in (0: not looked up yet)
+void *g_records_addr[kMaxDevices] = {};
+unsigned long long g_records_ctx[kMaxDevices] = {};
+
+// The id of the current CUDA context (unique for the life of the process),
+// through the driver's cuCtxGetCurrent and cuCtxGetId, reached by their
+// runtime entry points so that the library need not link the driver; false
+// if they are unavailable.
+bool current_context_id(unsigned long long *id) {
+  using GetCurrent = int (*)(void **);
+  using GetId = int (*)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  }
+  void *ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
 
 // The host-side name g_noalloc_records is only a stand-in for the symbol; the
-// device address comes from cudaGetSymbolAddress, once per device, with that
-// device current.
+// device address comes from cudaGetSymbolAddress, with the device current,
+// once per device and CUDA context (every call when the context's identity
+// cannot be read).
 cudaError_t records_on_device(int dev, void **addr) {
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_records_addr[dev]) {
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (!have_id || !g_records_addr[dev] || g_records_ctx[dev] != id) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_records);
     if (e != cudaSuccess) return e;
     g_records_addr[dev] = p;
+    g_records_ctx[dev] = have_id ? id : 0;
   }
   *addr = g_records_addr[dev];
   return cudaSuccess;
@@ -90,8 +133,8 @@ extern "C" veckm_status veckm_encode_noalloc(veckm_ctx *ctx, const int16_t *d_x,
       launch_scan(g, c.cnt, c.bsum, c.off, c.cur, c.total, s) < 0 ||
       launch_place(ev, g, c.cur, rec, rpix, s) < 0 ||
       launch_pixsum(g, c.tb, c.off + P, rec, rpix, n, c.acc, s) < 0 ||
-      launch_pool_rows(g, c.tb, c.acc, c.hbuf, s) < 0 ||
-      launch_pool_cols(g, c.tb, c.hbuf, c.acc, s) < 0 ||
+      launch_pool_rows(g, c.tb, c.acc, c.hbuf, s, c.tn) < 0 ||
+      launch_pool_cols(g, c.tb, c.hbuf, c.acc, s, c.tn) < 0 ||
       launch_counts(g, c.cnt, c.cnt_tmp, c.ncnt, s) < 0 ||
       launch_gather_emb(ev, d_K, nK, g, c.tb, c.acc, c.ncnt, d_emb, c.err, s) < 0)
     return report(VECKM_ECUDA, cudaGetErrorString(cudaGetLastError()));

@@ -58,4 +58,27 @@ __device__ __forceinline__ float4 time_phase2_lean(uint32_t t, uint2 w0, uint2 w
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// time_phase2_lean with the two channels' angles formed in one packed
+// FP32x2 fused multiply-add (the same rounding per lane, so the same angles).
+__device__ __forceinline__ float4 time_phase2_packed(uint32_t t, uint2 w0, uint2 w1) {
+  uint32_t f0, f1;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(f0) : "r"(t), "r"(w0.x), "r"(t * w0.y + 0x80000100u));
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(f1) : "r"(t), "r"(w1.x), "r"(t * w1.y + 0x80000100u));
+  const float x0 = __uint_as_float(__funnelshift_r(f0, 0x7fu, 9));
+  const float x1 = __uint_as_float(__funnelshift_r(f1, 0x7fu, 9));
+  const float2 tp = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
+  const float2 tc = make_float2(-9.42477796076937971538f, -9.42477796076937971538f);
+  const float2 x = make_float2(x0, x1);
+  uint64_t a;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(a)
+      : "l"(*reinterpret_cast<const uint64_t *>(&x)), "l"(*reinterpret_cast<const uint64_t *>(&tp)),
+        "l"(*reinterpret_cast<const uint64_t *>(&tc)));
+  const float2 ang = *reinterpret_cast<const float2 *>(&a);
+  float s0, c0, s1, c1;
+  __sincosf(ang.x, &s0, &c0);
+  __sincosf(ang.y, &s1, &c1);
+  return make_float4(c0, s0, c1, s1);
+}
+
 }  // namespace veckm

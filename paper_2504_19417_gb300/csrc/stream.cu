@@ -14,13 +14,16 @@
 // window's events alone.  Counts are exact int32.
 //
 // The stream's valid events live in a device ring (x, y, t; t in absolute
-// microseconds), in time order as long as packets arrive in time order and
-// are each sorted by time (event cameras emit them so; an event earlier than
-// its predecessor in the packet is rejected).  A packet is pushed with its
-// end time t_hi (every event has t <= t_hi); the window is then
-// [t_hi - window, t_hi].  A push, in stream order:
-//   1. flag the packet's valid events (inside the sensor and the window, in
-//      order) and scan the flags: the valid events' places in the ring;
+// microseconds), kept in time order: an event is accepted only if its time is
+// at least that of every event accepted before it, in earlier packets (the
+// stream's last accepted time) and earlier in its own packet (the running
+// maximum over the packet's in-range events before it), so the ring's times
+// ascend whatever order the events come in.  A packet is pushed with its end
+// time t_hi (every event has t <= t_hi; t_hi never goes back); the window is
+// then [t_hi - window, t_hi].  A push, in stream order:
+//   1. flag the packet's valid events (inside the sensor and the window, not
+//      earlier than an event accepted before them) and scan the flags: the
+//      valid events' places in the ring;
 //   2. find the first ring event still in the window (binary search) and how
 //      many valid events fit the ring after the expiry;
 //   3. subtract the events that left;
@@ -48,25 +51,125 @@ struct RingState {
   long long tail_old;  // the tail before the current push
   long long head_old;  // the head before the current push
   long long app;       // events of the current packet that fit the ring
+  unsigned t_last;     // time of the last accepted event (0 before the first)
 };
 
 __device__ __forceinline__ void red_add_s64(long long *p, long long v) {
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)v) : "memory");
 }
 
-// 1. valid events of the packet (inside the sensor and [t_lo, t_hi], not
-// earlier than the event before them)
+// 1a. events of the packet inside the sensor and [t_lo, t_hi]; tkey holds
+// their times (0 for the others), whose running maximum decides the order
 __global__ void k_ring_flags(const int16_t *__restrict__ x, const int16_t *__restrict__ y,
                              const uint32_t *__restrict__ t, long long n, int W, int H,
-                             uint32_t t_lo, uint32_t t_hi, int *__restrict__ flag, int *err) {
+                             uint32_t t_lo, uint32_t t_hi, int *__restrict__ flag,
+                             unsigned *__restrict__ tkey, int *err) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int xi = x[i], yi = y[i];
   const uint32_t ti = t[i];
-  const bool ok = xi >= 0 && xi < W && yi >= 0 && yi < H && ti >= t_lo && ti <= t_hi &&
-                  (i == 0 || t[i - 1] <= ti);
+  const bool ok = xi >= 0 && xi < W && yi >= 0 && yi < H && ti >= t_lo && ti <= t_hi;
   if (!ok) atomicOr(err, ERR_EVENT_RANGE);
   flag[i] = ok ? 1 : 0;
+  tkey[i] = ok ? ti : 0u;
+}
+
+// 1b. exclusive running maximum of tkey in blocks of kMaxBlock: per block
+// its maximum (reduce), the exclusive maximum over the blocks before each
+// (top, one CTA), then per event the maximum over the in-range events before
+// it; an in-range event earlier than that, or than the stream's last accepted
+// time, is out of order and not accepted.
+constexpr int kMaxThreads = 256;
+constexpr int kMaxPer = 4;
+constexpr int kMaxBlock = kMaxThreads * kMaxPer;
+
+// exclusive maximum of v over the threads before this one (0 for the first),
+// and the block's maximum in *total
+__device__ __forceinline__ unsigned block_excl_max(unsigned v, unsigned *s_warp, unsigned &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned m = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl = max(incl, m);
+  }
+  unsigned excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = 0u;
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+    unsigned wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned m = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi = max(wi, m);
+    }
+    unsigned we = __shfl_up_sync(0xffffffffu, wi, 1);
+    if (lane == 0) we = 0u;
+    s_warp[lane] = we;  // maximum over the warps before
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  const unsigned r = max(s_warp[warp], excl);
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_tmax_reduce(const unsigned *__restrict__ tkey,
+                                                             long long n,
+                                                             unsigned *__restrict__ bmax) {
+  __shared__ unsigned s_warp[33];
+  const long long b0 = (long long)blockIdx.x * kMaxBlock + threadIdx.x * kMaxPer;
+  unsigned v = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxPer; ++i)
+    if (b0 + i < n) v = max(v, tkey[b0 + i]);
+  unsigned total;
+  block_excl_max(v, s_warp, total);
+  if (threadIdx.x == 0) bmax[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_tmax_top(unsigned *__restrict__ bmax, int nb) {
+  __shared__ unsigned s_warp[33];
+  unsigned carry = 0;
+  for (int base = 0; base < nb; base += kMaxThreads) {
+    const int i = base + threadIdx.x;
+    const unsigned v = i < nb ? bmax[i] : 0u;
+    unsigned tot;
+    const unsigned ex = block_excl_max(v, s_warp, tot);
+    if (i < nb) bmax[i] = max(carry, ex);
+    carry = max(carry, tot);
+  }
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_tmax_order(const unsigned *__restrict__ tkey,
+                                                            long long n,
+                                                            const unsigned *__restrict__ bmax,
+                                                            const RingState *st,
+                                                            int *__restrict__ flag, int *err) {
+  __shared__ unsigned s_warp[33];
+  const long long b0 = (long long)blockIdx.x * kMaxBlock + threadIdx.x * kMaxPer;
+  unsigned k[kMaxPer];
+  unsigned v = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxPer; ++i) {
+    k[i] = b0 + i < n ? tkey[b0 + i] : 0u;
+    v = max(v, k[i]);
+  }
+  unsigned total;
+  unsigned run = max(max(block_excl_max(v, s_warp, total), bmax[blockIdx.x]), st->t_last);
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < kMaxPer; ++i) {
+    if (b0 + i < n && flag[b0 + i] && k[i] < run) {
+      flag[b0 + i] = 0;
+      bad = true;
+    }
+    run = max(run, k[i]);
+  }
+  if (bad) atomicOr(err, ERR_EVENT_RANGE);
 }
 
 // 2. new tail: the first ring event with t >= t_lo (ring events ascend in
@@ -159,8 +262,12 @@ __global__ void k_ring_append(const RingState *st, const int16_t *__restrict__ x
   K[i] = r;
 }
 
-__global__ void k_ring_advance(RingState *st) {
-  if (threadIdx.x == 0) st->head = st->head_old + st->app;
+// the ring's times ascend, so the last appended event holds the largest
+// accepted time
+__global__ void k_ring_advance(RingState *st, const uint32_t *__restrict__ rt, long long cap) {
+  if (threadIdx.x != 0) return;
+  st->head = st->head_old + st->app;
+  if (st->app > 0) st->t_last = rt[(st->head - 1) % cap];
 }
 
 // 6. the stream's FP32 grid for the pixels whose sums changed since the last
@@ -213,6 +320,9 @@ struct veckm_stream {
   int64_t *K = nullptr;
   RingState *st = nullptr;
   int *flag = nullptr, *off = nullptr, *cur = nullptr, *bsum = nullptr, *nvalid = nullptr;
+  unsigned *tkey = nullptr, *bmax = nullptr;
+  bool pushed = false;    // a packet (or an empty push) has set t_hi
+  uint32_t last_t_hi = 0; // t_hi of the last push
 };
 
 extern "C" {
@@ -244,6 +354,9 @@ veckm_status veckm_stream_create(veckm_ctx *c, int64_t window_us, int64_t capaci
   if (e == cudaSuccess) e = cudaMalloc(&s->cur, (size_t)capacity * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->bsum, (size_t)scan_blocks(capacity) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->nvalid, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->tkey, (size_t)capacity * 4);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&s->bmax, (size_t)((capacity + kMaxBlock - 1) / kMaxBlock) * 4);
   if (e == cudaSuccess) e = cudaMemset(s->acc64, 0, P * (size_t)c->g.U * 4 * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(s->accf, 0, P * (size_t)c->g.U * sizeof(float4));
   if (e == cudaSuccess) e = cudaMemset(s->dirty, 0, P);
@@ -267,6 +380,11 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   const Geometry &g = c->g;
   if (predict && g.D > 128 && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)))
     return fail_msg(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
+  if (s->pushed && t_hi_us < s->last_t_hi)
+    return fail_msg(VECKM_EINVAL, "t_hi %u is before the previous push's %u: a window never "
+                    "slides back", (unsigned)t_hi_us, (unsigned)s->last_t_hi);
+  s->pushed = true;
+  s->last_t_hi = t_hi_us;
   cudaStream_t cs = (cudaStream_t)stream;
   grids_dirty(c);  // the push pools through hbuf into acc
   const uint32_t t_lo = t_hi_us >= (uint64_t)s->window ? t_hi_us - (uint32_t)s->window : 0u;
@@ -283,7 +401,12 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   int launches = 0;
   // 1. valid events and their places
   if (n > 0) {
-    k_ring_flags<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(d_x, d_y, d_t, n, g.W, g.H, t_lo, t_hi_us, s->flag, c->err);
+    k_ring_flags<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(d_x, d_y, d_t, n, g.W, g.H, t_lo, t_hi_us, s->flag, s->tkey, c->err);
+    const int nbm = (int)((n + kMaxBlock - 1) / kMaxBlock);
+    k_tmax_reduce<<<nbm, kMaxThreads, 0, cs>>>(s->tkey, n, s->bmax);
+    k_tmax_top<<<1, kMaxThreads, 0, cs>>>(s->bmax, nbm);
+    k_tmax_order<<<nbm, kMaxThreads, 0, cs>>>(s->tkey, n, s->bmax, s->st, s->flag, c->err);
+    launches += 3;
     Geometry line{};
     line.W = (int)n;
     line.H = 1;
@@ -301,7 +424,7 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
     apply(+1);
     launches += 2;
   }
-  k_ring_advance<<<1, 32, 0, cs>>>(s->st);
+  k_ring_advance<<<1, 32, 0, cs>>>(s->st, s->rt, s->cap);
   launches += 1;
   cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) {
@@ -347,8 +470,10 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
     join.armed = false;
   }
   const Events ev{s->rx, s->ry, s->rt, s->cap, 0u, 0xffffffffu};
-  const bool half_grid = predict && (c->flags & VECKM_ACC_FP16);
+  const bool tc_head = predict && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16));
+  const bool half_grid = tc_head && (c->flags & VECKM_ACC_FP16);
   r = half_grid ? launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, cs, tn)
+      : tc_head ? launch_pool_cols_norm(g, tb, c->hbuf, c->ncnt, c->acc, cs, tn)
                 : launch_pool_cols(g, tb, c->hbuf, c->acc, cs, tn);
   if (r < 0) return fail_cuda(cudaGetLastError(), "pooling (columns) launch");
   launches += r;
@@ -393,7 +518,7 @@ void veckm_stream_destroy(veckm_stream *s) {
   if (!s) return;
   cudaDeviceSynchronize();
   void *ptrs[] = {s->acc64, s->accf, s->dirty, s->cnt, s->rx, s->ry, s->rt, s->K, s->st,
-                  s->flag, s->off, s->cur, s->bsum, s->nvalid};
+                  s->flag, s->off, s->cur, s->bsum, s->nvalid, s->tkey, s->bmax};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete s;

@@ -101,11 +101,42 @@ std::vector<uint16_t> w1_core_matrix(const std::vector<float> &W1, int hidden, i
   return out;
 }
 
+// W2 [2][hidden] as the B operand of the tensor-core head's second layer:
+// FP16, padded to 16 rows (rows 2..15 zero), K-major and 128-byte swizzled
+// like W1 (K-blocks of 64 columns, each 16 x 128 B), with the K axis in the
+// natural order of the hidden units.
+std::vector<uint16_t> w2_core_matrix(const std::vector<float> &W2, int hidden) {
+  constexpr int N2 = 16;
+  std::vector<uint16_t> out((size_t)N2 * hidden, 0);
+  for (int n = 0; n < 2; ++n)
+    for (int k = 0; k < hidden; ++k) {
+      const size_t byte = (size_t)(k / 64) * N2 * 128 + (size_t)(n / 8) * 1024 + (n % 8) * 128 +
+                          (size_t)((((k / 8) % 8) ^ (n % 8)) * 16) + (k % 8) * 2;
+      out[byte / 2] = half_bits(W2[(size_t)n * hidden + k], true);
+    }
+  return out;
+}
+
+// The tensor-core head rounds ReLU(h) to FP16 for its second layer.  An
+// encoding has |Re e_d|, |Im e_d| <= 1 (a mean of unit phasors), so
+// |h_j| <= sum_c |W1_jc| + |b1_j|; that must stay well inside FP16's range.
+bool tc_head_range_ok(const veckm_ctx *c) {
+  const int IN = 2 * c->g.D;
+  for (int j = 0; j < c->hidden; ++j) {
+    double s = std::fabs((double)c->hb1[j]);
+    for (int k = 0; k < IN; ++k) s += std::fabs((double)c->hW1[(size_t)j * IN + k]);
+    if (!(s < 32768.0)) return false;
+  }
+  for (float w : c->hW2)
+    if (!(std::fabs(w) < 32768.0f)) return false;
+  return true;
+}
+
 void free_all(veckm_ctx *c) {
   veckm::destroy_pipe(c->pipe);
   c->pipe = nullptr;
   void *ptrs[] = {c->tx, c->ty, c->sx, c->sy, c->wt, c->W1, c->W1t, c->b1, c->W2, c->b2,
-                  c->W1h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
+                  c->W1h, c->W2h, c->acc, c->hbuf, c->cnt, c->cnt_tmp, c->ncnt, c->err, c->st_buf,
                   c->off, c->cur, c->bsum, c->total, c->rec, c->rpix, c->brec, c->bhist, c->btot,
                   c->cx, c->cy, c->ct,
                   c->slice_tab, c->wxy, c->rx, c->ry};
@@ -339,10 +370,15 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   mark();
   join.wait();  // the window counts (side stream)
   mark();
-  // FP16 storage of the normalised pooled grid serves the tensor-core head only
-  const bool half_grid = what == Out::Flow && (c->flags & VECKM_ACC_FP16);
+  // The tensor-core head reads the pooled grid already divided by the window
+  // counts: FP16 (VECKM_ACC_FP16), else FP32 with each unit's real and
+  // imaginary parts paired; the other consumers read the plain window sums.
+  const bool tc_head = what == Out::Flow && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16));
+  const bool half_grid = tc_head && (c->flags & VECKM_ACC_FP16);
   if (half_grid)
     r = launch_pool_cols_half(g, tb, grow, c->ncnt, gsum, s, tn);
+  else if (tc_head)
+    r = launch_pool_cols_norm(g, tb, grow, c->ncnt, gsum, s, tn);
   else
     r = launch_pool_cols(g, tb, grow, gsum, s, tn);
   if (r < 0) return cuda_fail(cudaGetLastError(), "pooling (columns) launch");
@@ -500,6 +536,12 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   for (int h = 0; h < c->hidden; ++h)
     for (int k = 0; k < IN; ++k) hW1t[(size_t)k * c->hidden + h] = c->hW1[(size_t)h * IN + k];
   std::vector<uint16_t> hW1h = w1_core_matrix(c->hW1, c->hidden, IN, (c->flags & VECKM_MLP_FP16) != 0);
+  std::vector<uint16_t> hW2h = w2_core_matrix(c->hW2, c->hidden);
+  if ((c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16)) && !tc_head_range_ok(c)) {
+    delete c;
+    return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron: sum_c |W1_jc| + |b1_j| or |W2| "
+                "reaches 32768, beyond the FP16 range its second layer needs");
+  }
 
   const size_t P = (size_t)g.W * g.H;
   cudaError_t e = cudaSuccess;
@@ -523,6 +565,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(dalloc(&c->W1, (size_t)c->hidden * IN));
   VK_TRY(dalloc(&c->W1t, (size_t)c->hidden * IN));
   VK_TRY(dalloc(&c->W1h, (size_t)c->hidden * IN));
+  VK_TRY(dalloc(&c->W2h, hW2h.size()));
   VK_TRY(dalloc(&c->b1, (size_t)c->hidden));
   VK_TRY(dalloc(&c->W2, (size_t)2 * c->hidden));
   VK_TRY(dalloc(&c->b2, 2));
@@ -553,6 +596,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
   VK_TRY(cudaMemcpy(c->W1, c->hW1.data(), c->hW1.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1t, hW1t.data(), hW1t.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W1h, hW1h.data(), hW1h.size() * 2, cudaMemcpyHostToDevice));
+  VK_TRY(cudaMemcpy(c->W2h, hW2h.data(), hW2h.size() * 2, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->b1, cfg->h_b1, (size_t)c->hidden * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->W2, cfg->h_W2, (size_t)2 * c->hidden * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->b2, cfg->h_b2, 2 * 4, cudaMemcpyHostToDevice));
@@ -583,6 +627,9 @@ veckm_status veckm_set_mlp_mode(veckm_ctx *c, uint32_t flags) {
     return fail(VECKM_EINVAL, "bad flags 0x%x", flags);
   if ((flags & known) && c->g.D > 128)
     return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron supports D <= 128");
+  if ((flags & known) && !tc_head_range_ok(c))
+    return fail(VECKM_EUNSUPPORTED, "tensor-core perceptron: sum_c |W1_jc| + |b1_j| or |W2| "
+                "reaches 32768, beyond the FP16 range its second layer needs");
   if (flags & known) {
     std::vector<uint16_t> h = w1_core_matrix(c->hW1, c->hidden, 2 * c->g.D, (flags & VECKM_MLP_FP16) != 0);
     cudaError_t e = cudaDeviceSynchronize();
@@ -745,6 +792,7 @@ bool ctx_view(const veckm_ctx *c, CtxView *v) {
   v->total = c->total;
   v->err = c->err;
   v->t_span = c->t_span;
+  v->tn = c->tune_for(c->g);
   return true;
 }
 

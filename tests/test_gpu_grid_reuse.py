@@ -12,7 +12,8 @@ import pytest
 import oracle
 from paper_2504_19417_gb300 import synth
 from paper_2504_19417_gb300 import veckm as vk
-from tests.common import EMB_TOL_FP32, emb_rel_err, make, to_dev, within_half_bound
+from tests.common import (EMB_TOL_FP32, FLOW_FLOOR, FLOW_TOL, emb_rel_err, flow_rel_err, make,
+                          to_dev, within_half_bound)
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
@@ -36,8 +37,13 @@ def _check_predict(enc, sl, TXY, w, mode, K=None):
     Kd = None if K is None else torch.from_numpy(K).cuda()
     f = enc.predict(x, y, t, sl.t_ref, K=Kd).cpu().numpy()
     e = _emb_ref(sl, TXY, K)
-    r = within_half_bound(f, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, mode)
-    assert r <= 1.0, r
+    fref = oracle.mlp(e, w.W1, w.b1, w.W2, w.b2)
+    if mode == vk.MLP_FP32:
+        err = flow_rel_err(f, fref, FLOW_FLOOR)
+        assert err.max() <= FLOW_TOL[mode], err.max()
+    else:
+        r = within_half_bound(f, fref, e, w, mode)
+        assert r <= 1.0, r
 
 
 @pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_FP16 | vk.ACC_FP16, vk.MLP_BF16])
@@ -72,7 +78,8 @@ def test_every_path_between_predicts_leaves_the_next_one_correct():
     x, y, t = to_dev(sparse)
     f = enc.predict(x, y, t, sparse.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
     e = _emb_ref(sparse, TXY, K)
-    assert within_half_bound(f, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), e, w, vk.MLP_FP32) <= 1.0
+    err = flow_rel_err(f, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2), FLOW_FLOOR)
+    assert err.max() <= FLOW_TOL[vk.MLP_FP32], err.max()
     enc.set_path(vk.PATH_AUTO)
     predict_pair()
     # the FP32 head (no clearing)

@@ -278,12 +278,14 @@ def test_stage_timing_records_every_call():
     assert enc.last_launch_count() >= 4
 
 
-@pytest.mark.parametrize("mode", [vk.MLP_BF16, vk.MLP_FP32, vk.MLP_FP16 | vk.ACC_FP16])
+@pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_BF16, vk.MLP_FP32, vk.MLP_FP16 | vk.ACC_FP16])
 def test_full_size_640x480_sampled(mode):
     """The 640x480, 2M-event workload in the launch configuration the benchmark
-    times; the oracle computes a sample of the outputs one by one."""
+    times (MLP_FP16: FP32 pooled grid, FP16 tensor-core head, pooling shapes
+    autotuned); the oracle computes a sample of the outputs one by one."""
     sl, D = synth.workload("slice-640x480-2M")
     enc, TXY, w = make(sl, D, mode=mode)
+    enc.autotune(sl.width, sl.height)
     x, y, t = to_dev(sl)
     flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
     emb = enc.encode(x, y, t, sl.t_ref).cpu().numpy()

@@ -41,13 +41,14 @@ def test_recipe_matches_oracle_after_autotuning(name):
         assert emb_rel_err(emb, ref).max() <= EMB_TOL_FP32
         flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
         fref = oracle.mlp(ref, w.W1, w.b1, w.W2, w.b2)
-        # first-order propagation through the perceptron (Eq. 6) bounds each
-        # output by sum_j |W2_oj| (2u + u^2 + 1e-5) sum_c |W1_jc e_c| (plus
-        # the FP16-grid term); unlike a relative bar it does not tighten
-        # when an event's flow cancels
-        assert within_half_bound(flow, fref, ref, w, mode) <= 1.0
-        if mode == vk.MLP_FP32:  # the relative bar, as a measured summary
-            assert flow_rel_err(flow, fref, FLOW_FLOOR).mean() <= FLOW_TOL[mode]
+        if mode == vk.MLP_FP32:
+            # the FP32 bar: every event within 1e-4 relative to
+            # max(|flow|, FLOW_FLOOR median |flow|)
+            err = flow_rel_err(flow, fref, FLOW_FLOOR)
+            assert err.max() <= FLOW_TOL[mode], (err.max(), err.mean())
+        else:
+            # half operands: the a-priori rounding bound through Eq. 6
+            assert within_half_bound(flow, fref, ref, w, mode) <= 1.0
         enc.sync_status()
 
 

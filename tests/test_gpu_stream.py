@@ -170,3 +170,52 @@ def test_empty_pushes_slide_the_window():
     assert not acc.any() and not cnt.any()  # everything left: exactly zero
     enc.sync_status()
     st.close()
+
+
+def test_stream_keeps_time_order_within_and_across_packets():
+    # [10, 100, 50, 60]: 50 and 60 come after 100 and are both rejected; a
+    # packet whose first events are earlier than the last accepted one loses
+    # exactly those; a push whose t_hi goes back is refused on the host
+    W, H = 64, 48
+    enc, TXY, w = _enc(W, H)
+    st = vk.Stream(enc, WIN, 1_000)
+    base = 1_000_000
+    x = np.array([5, 6, 7, 8], np.int16)
+    y = np.array([9, 9, 9, 9], np.int16)
+    t = np.array([base + 10, base + 100, base + 50, base + 60], np.uint32)
+    e1 = st.push(_dev(x), _dev(y), _dev(t.view(np.int32)), base + 200, predict=False).cpu().numpy()
+    with pytest.raises(vk.VeckmError) as ei:
+        enc.sync_status()
+    assert ei.value.status == vk.VECKM_ERANGE
+    assert st.window_events() == 2
+    assert np.all(e1[2] == 0) and np.all(e1[3] == 0)
+    T, X, Y = TXY
+    ref = oracle.encode_pooled(x[:2], y[:2], t[:2], base, W, H, D, 10, 10, 16_000.0, T, X, Y)[0]
+    assert emb_rel_err(e1[:2], ref).max() <= EMB_TOL_FP32
+    # the next packet starts before 100, the last accepted time
+    x2 = np.array([10, 11, 12, 13], np.int16)
+    y2 = np.array([20, 20, 20, 20], np.int16)
+    t2 = np.array([base + 90, base + 99, base + 100, base + 150], np.uint32)
+    e2 = st.push(_dev(x2), _dev(y2), _dev(t2.view(np.int32)), base + 300, predict=False).cpu().numpy()
+    with pytest.raises(vk.VeckmError):
+        enc.sync_status()
+    assert st.window_events() == 4
+    assert np.all(e2[0] == 0) and np.all(e2[1] == 0)
+    xs = np.concatenate([x[:2], x2[2:]])
+    ys = np.concatenate([y[:2], y2[2:]])
+    ts = np.concatenate([t[:2], t2[2:]])
+    ref = oracle.encode_pooled(xs, ys, ts, base, W, H, D, 10, 10, 16_000.0, T, X, Y,
+                               K=np.array([2, 3], np.int64))[0]
+    assert emb_rel_err(e2[2:], ref).max() <= EMB_TOL_FP32
+    # the ring's sums equal those of its four events built afresh
+    acc, cnt = st.accumulator()
+    fresh = vk.Stream(enc, WIN, 1_000)
+    fresh.push(_dev(xs), _dev(ys), _dev(ts.view(np.int32)), base + 300, predict=False)
+    enc.sync_status()
+    acc2, cnt2 = fresh.accumulator()
+    assert np.array_equal(cnt, cnt2) and np.array_equal(acc, acc2)
+    with pytest.raises(vk.VeckmError) as ei:
+        st.push(_dev(x2[:0]), _dev(y2[:0]), _dev(t2[:0].view(np.int32)), base + 299, predict=False)
+    assert ei.value.status == vk.VECKM_EINVAL
+    st.close()
+    fresh.close()

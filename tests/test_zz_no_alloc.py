@@ -1,11 +1,15 @@
-"""veckm_encode_noalloc against veckm_encode, through the C ABI.
+"""veckm_encode_noalloc through the C ABI, against the FP64 oracle and against
+veckm_encode.
 
 veckm_encode_noalloc serves callers that may not allocate device memory
-while a call runs (graph recording, real-time loops, devices reserved up
-front): it keeps its per-event scratch in a fixed array that the library
-declares statically.  Its result must equal veckm_encode's within the FP32
-encoder bar, on consecutive calls that reuse the shared array.  This file is
-collected last so that a failure here never hides the other GPU tests.
+while a call runs: a loop with a real-time budget, which cannot wait for an
+allocation and the synchronisation before it, or a process that reserves
+all of a device's memory up front for its own allocator, where cudaMalloc
+fails.  It keeps its per-event scratch in a fixed array that the library
+declares statically.  Its result must match the oracle's pooled encoding
+(Eq. 16-17) and veckm_encode's within the FP32 encoder bar, on consecutive
+calls that reuse the shared array.  This file is collected last so that a
+failure here never hides the other GPU tests.
 """
 import ctypes as C
 
@@ -33,22 +37,31 @@ def _noalloc(enc, x, y, t, t_ref, K, nK, out):
 
 
 def test_noalloc_encode_matches_encode_on_consecutive_calls():
+    import oracle
     sl = synth.event_slice(346, 260, 20_000, 10_000, n_edges=8, seed=314)
-    enc, _, _ = make(sl, 64)
+    enc, (T, X, Y), _ = make(sl, 64)
     x, y, t = to_dev(sl)
     ref = enc.encode(x, y, t, sl.t_ref).cpu().numpy().astype(np.float64)
+    want = oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, 64, 10, 10,
+                                16_000.0, T, X, Y)[0]
+    assert emb_rel_err(ref, want).max() <= EMB_TOL_FP32
     for _ in range(2):
         out = torch.full((sl.n, 128), float("nan"), dtype=torch.float32, device="cuda")
         assert _noalloc(enc, x, y, t, sl.t_ref, None, sl.n, out) == vk.VECKM_OK
         torch.cuda.synchronize()
-        err = emb_rel_err(out.cpu().numpy(), ref)
+        got = out.cpu().numpy()
+        err = emb_rel_err(got, ref)
+        assert err.max() <= EMB_TOL_FP32, err.max()
+        err = emb_rel_err(got, want)
         assert err.max() <= EMB_TOL_FP32, err.max()
     # an explicit subset K, after a call of another size
     K = torch.arange(3, sl.n, 11, dtype=torch.int64, device="cuda")
     out = torch.empty((K.numel(), 128), dtype=torch.float32, device="cuda")
     assert _noalloc(enc, x, y, t, sl.t_ref, K, K.numel(), out) == vk.VECKM_OK
     torch.cuda.synchronize()
-    assert emb_rel_err(out.cpu().numpy(), ref[K.cpu().numpy()]).max() <= EMB_TOL_FP32
+    Kh = K.cpu().numpy()
+    assert emb_rel_err(out.cpu().numpy(), ref[Kh]).max() <= EMB_TOL_FP32
+    assert emb_rel_err(out.cpu().numpy(), want[Kh]).max() <= EMB_TOL_FP32
     enc.sync_status()
 
 
