@@ -548,6 +548,11 @@ def run_ours(args):
             out["sparse_k"] = sparse_leg(args, mode, stream)
         except Exception as e:  # the headline line is printed regardless
             out["sparse_k"] = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0 and not args.no_precision:
+        try:
+            out["precision"] = precision_leg(args, stream)
+        except Exception as e:  # the headline line is printed regardless
+            out["precision"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_recipes:
         try:
             out["recipes"] = recipes_leg(args, mode, stream)
@@ -711,6 +716,78 @@ def recipes_leg(args, mode, stream):
                                        "cols_seg": tuned[2], "cols_warps": tuned[3]}}
         enc.close()
     return out
+
+
+def precision_leg(args, stream):
+    """The precision workload: 1280x720, 4,000,000 events over 20 ms, D = 128,
+    a 256 -> 128 -> 2 head.  Per mode (FP32 or FP16 storage of the pooled
+    grid, BF16 or FP16 tensor-core head, and the plain FP32 form): the step
+    time, and the error per output against the FP64 oracle on a sample of
+    requested events (the oracle scatters every event and pools the sampled
+    ones, Algorithm 1): per flow component the largest and mean absolute
+    error, the flow error relative to max(|flow|, 0.25 median |flow|), and
+    the encoding's relative L2 error."""
+    import torch
+    import oracle
+    from paper_2504_19417_gb300 import synth
+    from paper_2504_19417_gb300 import veckm as vk
+    sl, D = synth.workload("slice-1280x720-4M")
+    T, X, Y = synth.frequencies(D, 0)
+    w = synth.mlp_weights(D, 128, 3)
+    p = vk.Params(width=sl.width, height=sl.height, D=D, dx=10, dy=10, dt_us=16_000,
+                  t_span_us=int(sl.t.max()) - sl.t_ref)
+    x = torch.from_numpy(sl.x).cuda()
+    y = torch.from_numpy(sl.y).cuda()
+    t = torch.from_numpy(sl.t.view(np.int32)).cuda()
+    flow = torch.empty((sl.n, 2), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(13)
+    S = args.precision_sample
+    K = np.sort(rng.choice(sl.n, S, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    emb_ref, _ = oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D, 10, 10,
+                                      16_000.0, T, X, Y, K=K)
+    flow_ref = oracle.mlp(emb_ref, w.W1, w.b1, w.W2, w.b2)
+    oracle_s = time.perf_counter() - t0
+    nr = np.linalg.norm(flow_ref, axis=1)
+    res = {"workload": f"slice-1280x720-4M ({sl.n} events, 20 ms, D={D}, 21x21, 256->128->2)",
+           "error_sample": f"{S} random requested events, FP64 oracle ({oracle_s:.1f} s)",
+           "modes": {}}
+    Kd = torch.from_numpy(K).cuda()
+    modes = (("bf16", vk.MLP_BF16), ("bf16-acc16", vk.MLP_BF16 | vk.ACC_FP16),
+             ("fp16", vk.MLP_FP16), ("fp16-acc16", vk.MLP_FP16 | vk.ACC_FP16),
+             ("fp32", vk.MLP_FP32))
+    enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=vk.MLP_BF16)
+    for name, m in modes:
+        enc.set_mlp_mode(m)
+        enc.autotune(sl.width, sl.height, stream)
+        k = max(3, args.steps // 4) if m != vk.MLP_FP32 else 3
+        for _ in range(args.warmup):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / k
+        enc.sync_status()
+        f = flow[Kd].cpu().numpy().astype(np.float64)
+        d = np.abs(f - flow_ref)
+        rel = np.linalg.norm(f - flow_ref, axis=1) / np.maximum(nr, 0.25 * np.median(nr))
+        res["modes"][name] = {
+            "ms_per_step": ms, "value": sl.n / (ms * 1e-3), "unit": UNIT,
+            "flow_abs_max": [float(d[:, 0].max()), float(d[:, 1].max())],
+            "flow_abs_mean": [float(d[:, 0].mean()), float(d[:, 1].mean())],
+            "flow_rel_max": float(rel.max()), "flow_rel_mean": float(rel.mean()),
+            "flow_rel_floor": "0.25 x median |flow|"}
+    emb = enc.encode(x, y, t, sl.t_ref, K=Kd).cpu().numpy().astype(np.float64)
+    e_err = np.linalg.norm(emb - emb_ref, axis=1) / np.linalg.norm(emb_ref, axis=1)
+    res["emb_rel_l2_max"] = float(e_err.max())
+    res["emb_rel_l2_mean"] = float(e_err.mean())
+    enc.sync_status()
+    enc.close()
+    return res
 
 
 def batch_leg(args, mode, stream):
@@ -902,6 +979,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-slice batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-recipes", action="store_true", help="skip the parameter-recipe leg")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 1280x720 D=128 precision leg")
+    ap.add_argument("--precision-sample", type=int, default=5_000)
     ap.add_argument("--no-autotune", action="store_true", help="default pooling launch shapes")
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-request leg")
     ap.add_argument("--no-stream", action="store_true", help="skip the sliding-window leg")

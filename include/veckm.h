@@ -430,6 +430,34 @@ veckm_status veckm_server_get_stats(veckm_server *srv, veckm_server_stats *st);
 /* Stops the worker after the packets in flight and frees everything. */
 void veckm_server_destroy(veckm_server *srv);
 
+/* ------------------------------------------------------------ error paths
+ * Failure detection and its tests (not in the paper).  Every wait of a
+ * kernel on another part of itself (the tensor-core head's mbarrier
+ * hand-offs) is bounded: when it runs out the kernel releases what it holds
+ * and leaves, the rows it did not finish keep whatever they held, and the
+ * device error word reports VECKM_ETIMEOUT at the next status check; the
+ * context stays usable. */
+
+/* Limit of each bounded wait of the tensor-core head in SM clock cycles;
+ * 0 restores the default (4e9 cycles, about 2 s at 2 GHz). */
+veckm_status veckm_set_wait_limit(veckm_ctx *ctx, int64_t cycles);
+
+/* Fault injection for tests of the error paths, off by default.
+ * VECKM_INJECT_HEAD_STALL: the tensor-core head's producer warps never signal
+ * a filled tile, so its waits run out (VECKM_ETIMEOUT); nothing faults and
+ * nothing waits without a limit.  VECKM_INJECT_NONE turns it off. */
+#define VECKM_INJECT_NONE 0
+#define VECKM_INJECT_HEAD_STALL 1
+veckm_status veckm_set_injection(veckm_ctx *ctx, int32_t what);
+
+/* Test hook for the out-of-memory paths (host side): counts the library's
+ * device (cudaMalloc) and pinned host (cudaMallocHost) allocations from 0
+ * again, and makes allocation number fail_at (if >= 0; -1 turns it off) fail
+ * as if memory were exhausted, which the calling entry point reports as
+ * VECKM_ENOMEM after freeing what it had allocated.  Returns the number of
+ * allocations counted since the previous call.  Process wide. */
+int64_t veckm_debug_fail_alloc(int64_t fail_at);
+
 /* SplitMix64 + Box-Muller standard normals (the generator behind freq_seed):
  * writes count normals of stream `seed` to h_out.  Host only. */
 void veckm_normals(uint64_t seed, int64_t count, double *h_out);

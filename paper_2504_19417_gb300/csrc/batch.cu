@@ -158,7 +158,7 @@ template <typename T>
 cudaError_t grow(T **p, int64_t count) {
   if (*p) cudaFree(*p);
   *p = nullptr;
-  return cudaMalloc(reinterpret_cast<void **>(p), (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+  return dev_malloc(reinterpret_cast<void **>(p), (size_t)std::max<int64_t>(count, 1) * sizeof(T));
 }
 
 // Canvas event buffers, the device slice table and the records for p.
@@ -218,7 +218,7 @@ veckm_status batch_call(veckm_ctx *c, const veckm_slice *sl, int32_t ns, float *
     if (c->h_slice_tab) cudaFreeHost(c->h_slice_tab);
     c->h_slice_tab = nullptr;
     c->h_slice_tab_cap = 0;
-    e = cudaMallocHost(&c->h_slice_tab, bytes);
+    e = host_malloc(reinterpret_cast<void **>(&c->h_slice_tab), bytes);
     if (e == cudaSuccess) c->h_slice_tab_cap = bytes;
   }
   if (e == cudaSuccess && !c->tab_copied)
@@ -397,7 +397,7 @@ veckm_status veckm_plan_create(veckm_ctx *c, const veckm_slice *sl, int32_t ns, 
   if (st == VECKM_OK && p.N > 0 && !tuned_for(c, p.g)) st = autotune(c, p.g, cs, nullptr);
   const size_t bytes = p.tab.size() * sizeof(SliceDev);
   if (st == VECKM_OK && p.N > 0) {
-    e = cudaMallocHost(&pl->h_tab, std::max<size_t>(bytes, 1));
+    e = host_malloc(reinterpret_cast<void **>(&pl->h_tab), std::max<size_t>(bytes, 1));
     if (e != cudaSuccess) st = fail_cuda(e, "plan slice table");
     else std::memcpy(pl->h_tab, p.tab.data(), bytes);
   }

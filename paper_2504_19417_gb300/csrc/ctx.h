@@ -10,6 +10,7 @@
 namespace veckm {
 struct HostPipe;  // pipelined host-buffer calls (host_async.cu)
 constexpr int kStages = 6;  // sort, pixel sums, pool rows, counts, pool cols, gather
+constexpr long long kDefaultWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 }  // namespace veckm
 
 struct veckm_ctx {
@@ -91,6 +92,9 @@ struct veckm_ctx {
   // of the direct form, measured on GB300 (0.5 M events, 10 k flows, 640x480,
   // 17x17 window; settable with veckm_set_path_model)
   int path = VECKM_PATH_AUTO, last_path = 0;
+  // bounded device waits of the tensor-core head, and the test injection
+  long long wait_cycles = veckm::kDefaultWaitCycles;
+  int inject = VECKM_INJECT_NONE;
   double k_pixel = 0.43e-9, k_flow_dense = 1.53e-9, k_flow_window = 0.077e-9;
 
   veckm::Tables tables() const { return veckm::Tables{tx, ty, sx, sy, wt, rx, ry}; }
@@ -101,7 +105,8 @@ struct veckm_ctx {
   }
   veckm::MLP mlp() const {
     return veckm::MLP{W1,     W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0,
-                      hb1.data(), hW2.data(), hb2.data(), W2h};
+                      hb1.data(), hW2.data(), hb2.data(), W2h, wait_cycles,
+                      inject == VECKM_INJECT_HEAD_STALL ? 1 : 0};
   }
 };
 

@@ -101,7 +101,7 @@ veckm_status veckm_predict_host_async(veckm_ctx *c, const int16_t *hx, const int
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.up, cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.down, cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaMallocHost(&s.h_err, sizeof(int));
+      if (e == cudaSuccess) e = host_malloc(reinterpret_cast<void **>(&s.h_err), sizeof(int));
     }
     if (e != cudaSuccess) {
       destroy_pipe(p);
@@ -121,7 +121,7 @@ veckm_status veckm_predict_host_async(veckm_ctx *c, const int16_t *hx, const int
     if (s.buf) cudaFree(s.buf);
     s.buf = nullptr;
     s.cap = 0;
-    e = cudaMalloc(&s.buf, std::max<size_t>(need, 256));
+    e = dev_malloc(reinterpret_cast<void **>(&s.buf), std::max<size_t>(need, 256));
     if (e != cudaSuccess) return fail_cuda(e, "staging buffers");
     s.cap = need;
   }

@@ -92,7 +92,6 @@ struct __align__(16) EpiParams {
 // row k; -1 writes nothing; k <= -2 writes zeros to row -2 - k (an invalid
 // event or index).
 __device__ __forceinline__ int invalid_row(int i) { return -2 - i; }
-constexpr long long kWaitLimitCycles = 4000000000LL;  // ~2 s at 2 GHz, then give up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -131,8 +130,8 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fp16) {
 // Waits for the phase with the given parity.  try_wait suspends the thread
 // in hardware until the phase completes or the hint (ns) runs out, so a
 // waiting warp takes no issue slots from the warps doing the work; the loop
-// gives up after kWaitLimitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// gives up after `limit` SM cycles (the context's wait limit).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
@@ -143,7 +142,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity), "r"(1000000u)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kWaitLimitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -258,6 +257,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int fp16 = F16 ? 1 : 0;
+  const long long wl = mlp.wait_cycles;
 
   {  // W1 and W2 (already in SW128 order)
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ((lane >> 4) * kHalfLines + l) * 128));
       }
       pf_load(tile + 3 * (int)gridDim.x);
-      if (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1)) {
+      if (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1, wl)) {
         ok = false;
         break;
       }
@@ -518,7 +518,8 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(full_bar(b));
+      // (the stall injection of the error-path tests withholds this signal)
+      if (lane == 0 && !mlp.inject_stall) mbar_arrive(full_bar(b));
       c_outk = n_outk;
       c_inv = n_inv;
     }
@@ -550,13 +551,13 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       const int b = li & 1;
       const uint32_t par = (li >> 1) & 1;
       // full: the producers' tile and row metadata
-      if (!mbar_wait(full_bar(b), par)) {
+      if (!mbar_wait(full_bar(b), par, wl)) {
         ok = false;
         break;
       }
       if (warp == kMmaWarp) {
         // accumulator b is free once all epilogue warps have read tile li - 2
-        if (li >= 2 && !mbar_wait(empty_bar(b), par ^ 1)) {
+        if (li >= 2 && !mbar_wait(empty_bar(b), par ^ 1, wl)) {
           ok = false;
           break;
         }
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         __syncwarp();
       }
       // done: the first layer's accumulator
-      if (!mbar_wait(done_bar(b), par)) {
+      if (!mbar_wait(done_bar(b), par, wl)) {
         ok = false;
         break;
       }
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       if (lane == 0) mbar_arrive(stored_bar(b));
       if (warp == kMmaWarp) {
         // the second layer once every epilogue warp has stored its rows
-        if (!mbar_wait(stored_bar(b), par)) {
+        if (!mbar_wait(stored_bar(b), par, wl)) {
           ok = false;
           break;
         }
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         }
         __syncwarp();
       }
-      if (!mbar_wait(out_bar(b), par)) {
+      if (!mbar_wait(out_bar(b), par, wl)) {
         ok = false;
         break;
       }
@@ -677,8 +678,8 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     if (!ok) {
       // let MMAs that may still be in flight land before their TMEM is freed
       for (int b = 0; b < 2; ++b) {
-        mbar_wait(done_bar(b), 0), mbar_wait(done_bar(b), 1);
-        mbar_wait(out_bar(b), 0), mbar_wait(out_bar(b), 1);
+        mbar_wait(done_bar(b), 0, wl), mbar_wait(done_bar(b), 1, wl);
+        mbar_wait(out_bar(b), 0, wl), mbar_wait(out_bar(b), 1, wl);
       }
     }
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),

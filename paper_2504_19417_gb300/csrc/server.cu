@@ -305,15 +305,15 @@ veckm_status veckm_server_create(const veckm_server_config *cfg, veckm_server **
   s->window = std::chrono::microseconds(std::max(0, cfg->batch_window_us));
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < kMaxInflight && e == cudaSuccess; ++i)
-    e = cudaMalloc(&s->d_flow[i], (size_t)s->max_events * 8);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_err, kMaxInflight * sizeof(int));
+    e = veckm::dev_malloc(reinterpret_cast<void **>(&s->d_flow[i]), (size_t)s->max_events * 8);
+  if (e == cudaSuccess) e = veckm::host_malloc(reinterpret_cast<void **>(&s->h_err), kMaxInflight * sizeof(int));
   int64_t arena = cfg->arena_bytes;
   if (e == cudaSuccess && arena == 0) {
     size_t free_b = 0, total_b = 0;
     e = cudaMemGetInfo(&free_b, &total_b);
     arena = (int64_t)(free_b / 4) & ~int64_t(255);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&s->arena, (size_t)std::max<int64_t>(arena, 256));
+  if (e == cudaSuccess) e = veckm::dev_malloc(reinterpret_cast<void **>(&s->arena), (size_t)std::max<int64_t>(arena, 256));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->comp, cudaStreamNonBlocking);
   if (e != cudaSuccess) {

@@ -340,23 +340,23 @@ veckm_status veckm_stream_create(veckm_ctx *c, int64_t window_us, int64_t capaci
   s->window = window_us;
   s->cap = capacity;
   const size_t P = (size_t)c->g.W * c->g.H;
-  cudaError_t e = cudaMalloc(&s->acc64, P * (size_t)c->g.U * 4 * sizeof(long long));
-  if (e == cudaSuccess) e = cudaMalloc(&s->accf, P * (size_t)c->g.U * sizeof(float4));
-  if (e == cudaSuccess) e = cudaMalloc(&s->dirty, P);
-  if (e == cudaSuccess) e = cudaMalloc(&s->cnt, P * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&s->rx, (size_t)capacity * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&s->ry, (size_t)capacity * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&s->rt, (size_t)capacity * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->K, (size_t)capacity * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(RingState));
-  if (e == cudaSuccess) e = cudaMalloc(&s->flag, (size_t)capacity * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->off, ((size_t)capacity + 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->cur, (size_t)capacity * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->bsum, (size_t)scan_blocks(capacity) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->nvalid, 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->tkey, (size_t)capacity * 4);
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&s->acc64), P * (size_t)c->g.U * 4 * sizeof(long long));
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->accf), P * (size_t)c->g.U * sizeof(float4));
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->dirty), P);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->cnt), P * sizeof(int));
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->rx), (size_t)capacity * 2);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->ry), (size_t)capacity * 2);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->rt), (size_t)capacity * 4);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->K), (size_t)capacity * 8);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->st), sizeof(RingState));
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->flag), (size_t)capacity * 4);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->off), ((size_t)capacity + 1) * 4);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->cur), (size_t)capacity * 4);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->bsum), (size_t)scan_blocks(capacity) * 4);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->nvalid), 4);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&s->tkey), (size_t)capacity * 4);
   if (e == cudaSuccess)
-    e = cudaMalloc(&s->bmax, (size_t)((capacity + kMaxBlock - 1) / kMaxBlock) * 4);
+    e = dev_malloc(reinterpret_cast<void **>(&s->bmax), (size_t)((capacity + kMaxBlock - 1) / kMaxBlock) * 4);
   if (e == cudaSuccess) e = cudaMemset(s->acc64, 0, P * (size_t)c->g.U * 4 * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(s->accf, 0, P * (size_t)c->g.U * sizeof(float4));
   if (e == cudaSuccess) e = cudaMemset(s->dirty, 0, P);

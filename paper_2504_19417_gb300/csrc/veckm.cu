@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,6 +16,19 @@
 #include <vector>
 
 #include "ctx.h"
+
+namespace veckm {
+namespace {
+// the allocation counter behind veckm_debug_fail_alloc
+std::atomic<long long> g_alloc_count{0};     // allocations since the last reset
+std::atomic<long long> g_alloc_fail_at{-1};  // the one to fail (-1: none)
+
+bool alloc_should_fail() {
+  const long long k = g_alloc_count.fetch_add(1);
+  return k == g_alloc_fail_at.load();
+}
+}  // namespace
+}  // namespace veckm
 
 using namespace veckm;
 
@@ -51,7 +65,7 @@ namespace {
 
 template <typename T>
 cudaError_t dalloc(T **p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+  return dev_malloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
 }
 
 // exp(i (first + n) * step * w_d * scale) for n in [0, rows) as interleaved
@@ -207,7 +221,15 @@ veckm_status ensure_records(veckm_ctx *c, int64_t n, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->rec, (size_t)n);
   if (e == cudaSuccess) e = dalloc(&c->rpix, (size_t)n);
   if (e == cudaSuccess) e = dalloc(&c->brec, (size_t)n);
-  if (e != cudaSuccess) return cuda_fail(e, "event record buffers");
+  if (e != cudaSuccess) {  // keep none of a partial set
+    if (c->rec) cudaFree(c->rec);
+    if (c->rpix) cudaFree(c->rpix);
+    if (c->brec) cudaFree(c->brec);
+    c->rec = nullptr;
+    c->rpix = nullptr;
+    c->brec = nullptr;
+    return cuda_fail(e, "event record buffers");
+  }
   c->rec_cap = n;
   return VECKM_OK;
 }
@@ -584,7 +606,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
     VK_TRY(dalloc(&c->btot, nbmax));
   }
   VK_TRY(dalloc(&c->err, 1));
-  VK_TRY(cudaMallocHost(reinterpret_cast<void **>(&c->h_err), sizeof(int)));
+  VK_TRY(host_malloc(reinterpret_cast<void **>(&c->h_err), sizeof(int)));
   VK_TRY(cudaMemcpy(c->tx, htx.data(), htx.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->ty, hty.data(), hty.size() * 4, cudaMemcpyHostToDevice));
   VK_TRY(cudaMemcpy(c->sx, hsx.data(), hsx.size() * 4, cudaMemcpyHostToDevice));
@@ -616,6 +638,27 @@ void veckm_destroy(veckm_ctx *c) {
   cudaDeviceSynchronize();
   free_all(c);
   delete c;
+}
+
+int64_t veckm_debug_fail_alloc(int64_t fail_at) {
+  const long long n = veckm::g_alloc_count.exchange(0);
+  veckm::g_alloc_fail_at.store(fail_at >= 0 ? fail_at : -1);
+  return n;
+}
+
+veckm_status veckm_set_wait_limit(veckm_ctx *c, int64_t cycles) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  if (cycles < 0) return fail(VECKM_EINVAL, "negative wait limit");
+  c->wait_cycles = cycles > 0 ? cycles : kDefaultWaitCycles;
+  return VECKM_OK;
+}
+
+veckm_status veckm_set_injection(veckm_ctx *c, int32_t what) {
+  if (!c) return fail(VECKM_EINVAL, "null context");
+  if (what != VECKM_INJECT_NONE && what != VECKM_INJECT_HEAD_STALL)
+    return fail(VECKM_EINVAL, "unknown injection %d", what);
+  c->inject = what;
+  return VECKM_OK;
 }
 
 veckm_status veckm_set_mlp_mode(veckm_ctx *c, uint32_t flags) {
@@ -683,7 +726,7 @@ veckm_status veckm_predict_host(veckm_ctx *c, const int16_t *hx, const int16_t *
     if (c->st_buf) cudaFree(c->st_buf);
     c->st_buf = nullptr;
     c->st_cap = 0;
-    if (e == cudaSuccess) e = cudaMalloc(&c->st_buf, need);
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&c->st_buf), need);
     if (e != cudaSuccess) return cuda_fail(e, "staging buffers");
     c->st_cap = need;
   }
@@ -797,6 +840,22 @@ bool ctx_view(const veckm_ctx *c, CtxView *v) {
 }
 
 veckm_status report(veckm_status st, const char *msg) { return fail(st, "%s", msg); }
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc(void **p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
 
 void grids_dirty(veckm_ctx *c) {
   if (c) c->zero_grid = -1;

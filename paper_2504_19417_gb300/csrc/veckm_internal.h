@@ -53,6 +53,10 @@ struct MLP {
   // [16][hidden] FP16 bits: W2 padded to 16 rows, core-matrix order for
   // the tensor-core head's second layer
   const uint16_t *W2h = nullptr;
+  // tensor-core head: limit of each bounded wait in SM cycles, and the test
+  // injection that stops its producers from signalling filled tiles
+  long long wait_cycles = 4000000000LL;
+  int inject_stall = 0;
 };
 
 // Launch shapes picked by the autotuner (batch.cu); 0 keeps the built-in
@@ -162,5 +166,11 @@ struct CtxView {
 bool ctx_view(const veckm_ctx *c, CtxView *v);
 // Records msg as this thread's last error and returns st.
 veckm_status report(veckm_status st, const char *msg);
+
+// Every device (dev_malloc) and pinned-host (host_malloc) allocation of the
+// library goes through these: they count allocations and can fail one of them
+// on purpose (veckm_debug_fail_alloc) to test the out-of-memory paths.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t host_malloc(void **p, size_t bytes);
 
 }  // namespace veckm

@@ -81,7 +81,15 @@ EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noallo
            "veckm_server_get_stats", "veckm_server_destroy", "veckm_kde_query", "veckm_set_path",
            "veckm_last_path", "veckm_set_path_model", "veckm_stream_create", "veckm_stream_push",
            "veckm_stream_window", "veckm_stream_accumulator", "veckm_stream_destroy",
+           "veckm_set_wait_limit", "veckm_set_injection", "veckm_debug_fail_alloc",
            "veckm_normals")
+INJECT_NONE, INJECT_HEAD_STALL = 0, 1
+
+
+def debug_fail_alloc(fail_at: int) -> int:
+    """Counts the library's allocations from 0 again and fails allocation
+    number fail_at (-1: none); returns the count since the previous call."""
+    return int(lib().veckm_debug_fail_alloc(fail_at))
 
 
 def library_path() -> str:
@@ -112,6 +120,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_set_timing.argtypes = [P, i32]
     lib.veckm_stage_times.argtypes = [P, P, P, i32]
     lib.veckm_last_launch_count.argtypes = [P]
+    lib.veckm_set_wait_limit.argtypes = [P, i64]
+    lib.veckm_set_injection.argtypes = [P, i32]
+    lib.veckm_debug_fail_alloc.argtypes = [i64]
+    lib.veckm_debug_fail_alloc.restype = i64
     lib.veckm_normals.argtypes = [C.c_uint64, i64, P]
     lib.veckm_normals.restype = None
     i32 = C.c_int32
@@ -583,6 +595,12 @@ class Encoder:
 
     def set_path(self, path: int):
         _check(lib().veckm_set_path(self._h, path))
+
+    def set_wait_limit(self, cycles: int):
+        _check(lib().veckm_set_wait_limit(self._h, cycles))
+
+    def set_injection(self, what: int):
+        _check(lib().veckm_set_injection(self._h, what))
 
     def last_path(self) -> int:
         return int(lib().veckm_last_path(self._h))

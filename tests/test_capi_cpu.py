@@ -76,3 +76,31 @@ def test_calls_on_null_context_are_rejected():
     assert L.veckm_predict(None, None, None, None, 0, 0, None, 0, None, None) == vk.VECKM_EINVAL
     assert L.veckm_sync_status(None, None) == vk.VECKM_EINVAL
     L.veckm_destroy(None)  # NULL-safe
+
+
+def test_error_path_hooks_validate_on_host():
+    L = vk.lib()
+    assert L.veckm_set_injection(None, vk.INJECT_HEAD_STALL) == vk.VECKM_EINVAL
+    assert L.veckm_set_wait_limit(None, 1000) == vk.VECKM_EINVAL
+    # the allocation counter: reset, no allocation happens on a rejected
+    # create (host-side checks come first), reset again
+    vk.debug_fail_alloc(-1)
+    c, keep = _cfg(width=0)
+    h = C.c_void_p()
+    assert L.veckm_create(C.byref(h), C.byref(c)) == vk.VECKM_EINVAL
+    assert vk.debug_fail_alloc(-1) == 0
+
+
+def test_tensor_core_head_rejects_weights_beyond_fp16_range():
+    # |h_j| <= sum_c |W1_jc| + |b1_j| must stay inside the FP16 range of the
+    # second layer's operand
+    w = synth.mlp_weights(64)
+    W1 = w.W1.copy()
+    W1[5, :] = 1000.0
+    c, keep = _cfg(flags=vk.MLP_FP16)
+    keep.append(W1)
+    c.h_W1 = W1.ctypes.data_as(C.c_void_p)
+    h = C.c_void_p()
+    assert vk.lib().veckm_create(C.byref(h), C.byref(c)) == vk.VECKM_EUNSUPPORTED
+    assert not h.value
+    assert b"FP16" in vk.lib().veckm_last_error()
