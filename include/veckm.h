@@ -365,17 +365,32 @@ veckm_status veckm_stream_accumulator(veckm_stream *st, int64_t *h_acc, int32_t 
 void veckm_stream_destroy(veckm_stream *st);
 
 /* ------------------------------------------------------------------ serving
- * A request loop for event packets from many sensors.  Each packet is one
- * slice (its events, its sensor size and its start).  veckm_server_submit
+ * A request loop for event packets from many sensors.  veckm_server_submit
  * admits a packet if its events (8 bytes each, in three 256-byte aligned
- * arrays) fit in the server's device arena, a ring sized
- * from free HBM at creation, and refuses it with VECKM_EBUSY otherwise; an
- * admitted packet's events are copied host-to-device at once on an upload
- * stream.  A native worker thread takes admitted packets in arrival order,
- * as many as fit one canvas batch, runs them as one veckm_predict_batch on
- * its compute stream (at most two batches in flight), copies each packet's
- * flows to its host buffer and reports the packet complete, with its latency
- * from submission to completion.  The paper has no serving layer. */
+ * arrays; with resident windows also its flows, 8 bytes each) fit in the
+ * server's device arena, a ring sized from free HBM at creation, and refuses
+ * it with VECKM_EBUSY otherwise; an admitted packet's events are copied
+ * host-to-device at once on an upload stream.  A native worker thread takes
+ * admitted packets in arrival order.  Two modes:
+ *   - packets as slices (window_us == 0): each packet is one slice (its
+ *     events, its sensor size and its start).  The worker takes as many
+ *     waiting packets as fit one canvas batch and runs them as one
+ *     veckm_predict_batch on its compute stream (at most two batches in
+ *     flight).
+ *   - resident windows (window_us > 0): every sensor stream keeps its
+ *     window's per-pixel sums resident on the device (a veckm_stream of its
+ *     own, on a context of its own sensor size, created with the stream's
+ *     first packet; a stream whose state cannot be allocated has its packet
+ *     refused with VECKM_EBUSY).  A packet of a stream slides that stream's
+ *     window to end at its last event (events must come sorted by time, not
+ *     earlier than the stream's previous ones; t_ref_us is unused) and its
+ *     flows are those of its events against the window (veckm_stream_push).
+ *     Each stream's packets run in order on the stream's own CUDA stream;
+ *     packets of different streams run concurrently on the device, up to 64
+ *     at once, and complete in any order.
+ * Each packet's flows are copied to its host buffer and the packet is
+ * reported complete, with its latency from submission to completion.  The
+ * paper has no serving layer. */
 typedef struct veckm_server veckm_server;
 
 typedef struct {
@@ -386,6 +401,9 @@ typedef struct {
     int64_t max_batch_events;  /* events per batch; 0: 2^24 */
     int32_t batch_window_us;   /* a batch that is not full waits for more packets until
                                   its oldest packet is this old; 0: launch at once */
+    int32_t window_us;         /* > 0: resident windows of this length per stream; 0:
+                                  packets as slices */
+    int64_t window_capacity;   /* events one stream's window may hold; 0: 2^22 */
 } veckm_server_config;
 
 typedef struct {
@@ -412,7 +430,8 @@ typedef struct {
     int64_t submitted, admitted, refused, completed, batches, events_completed, streams;
     double p50_ms, p99_ms, max_ms;  /* latency over completed packets */
     double wall_s;                  /* first submission to last completion */
-    double gpu_busy_s;              /* sum of batch device times (CUDA events) */
+    double gpu_busy_s;              /* sum of batch device times (CUDA events); with resident
+                                       windows, of per-packet device times, which overlap */
 } veckm_server_stats;
 
 /* Create the server, its context (cfg->model) and its worker thread.  The

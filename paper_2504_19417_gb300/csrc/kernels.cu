@@ -865,7 +865,14 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     auto emit = [&](int j, int qs, const float4 *G) {
       const int pos = o0 + j;
       float inv = 0.f;
-      if (NORM) inv = __shfl_sync(kFull, inv_lane, j - j0);
+      if (NORM) {
+        if (L <= 32) {
+          inv = __shfl_sync(kFull, inv_lane, j - j0);
+        } else {  // a block longer than the warp: the count of this output itself
+          const int c = __ldg(ncnt + (size_t)pos * g.W + line);
+          inv = c > 0 ? 1.0f / (float)c : 0.f;
+        }
+      }
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
         const int u = lane + 32 * v;

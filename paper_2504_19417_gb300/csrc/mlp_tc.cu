@@ -130,9 +130,12 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fp16) {
 // Waits for the phase with the given parity.  try_wait suspends the thread
 // in hardware until the phase completes or the hint (ns) runs out, so a
 // waiting warp takes no issue slots from the warps doing the work; the loop
-// gives up after `limit` SM cycles (the context's wait limit).
+// gives up after `limit` SM cycles (the context's wait limit).  Called by
+// whole warps; the answer is the same for every lane (false if any lane gave
+// up), so that no lane leaves a loop its warp mates stay in.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
+  bool done;
   while (true) {
     uint32_t ok;
     asm volatile(
@@ -141,9 +144,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
         : "=r"(ok)
         : "r"(bar), "r"(parity), "r"(1000000u)
         : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > limit) return false;
+    if (ok) {
+      done = true;
+      break;
+    }
+    if (clock64() - t0 > limit) {
+      done = false;
+      break;
+    }
   }
+  return __all_sync(0xffffffffu, done);
+}
+
+// Whether the phase with the given parity has completed (no waiting); the
+// same answer for the whole warp (lane 0's).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 // a * b and a - b on two FP32 lanes at once (packed FP32x2, one instruction)
@@ -547,6 +570,33 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       for (int64_t u = a + row; u < e; u += kEpiWarps * 32) zero_buf[u] = make_float4(0.f, 0.f, 0.f, 0.f);
     };
     int zeroed = 0;  // slices this thread has cleared
+    // first layer of tile i into accumulator i & 1 (warp kMmaWarp)
+    auto issue_l1 = [&](int i) {
+      if (lane == 0) {
+        const int bi = i & 1;
+        const uint32_t d_tmem = tmem + (uint32_t)(bi * kN);
+        const uint32_t a_base = sA_a + bi * TILE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < IN / 16; ++kk) {
+          // K-step kk: K-block kk / 4, 32-byte step kk % 4 inside the swizzle atom
+          const uint32_t koff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
+          const uint64_t ad = make_desc_sw128(a_base + koff);
+          const uint64_t bd = make_desc_sw128(sB_a + koff);
+          const uint32_t acc = kk > 0 ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                done_bar(bi))
+            : "memory");
+      }
+      __syncwarp();
+    };
+    int early = -1;  // warp kMmaWarp: the tile whose first layer went out early
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
       const uint32_t par = (li >> 1) & 1;
@@ -555,35 +605,14 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         ok = false;
         break;
       }
-      if (warp == kMmaWarp) {
+      if (warp == kMmaWarp && early != li) {
         // accumulator b is free once all epilogue warps have read tile li - 2
         if (li >= 2 && !mbar_wait(empty_bar(b), par ^ 1, wl)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (lane == 0) {
-          const uint32_t d_tmem = tmem + (uint32_t)(b * kN);
-          const uint32_t a_base = sA_a + b * TILE_BYTES;
-#pragma unroll
-          for (int kk = 0; kk < IN / 16; ++kk) {
-            // K-step kk: K-block kk / 4, 32-byte step kk % 4 inside the swizzle atom
-            const uint32_t koff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
-            const uint64_t ad = make_desc_sw128(a_base + koff);
-            const uint64_t bd = make_desc_sw128(sB_a + koff);
-            const uint32_t acc = kk > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
-          }
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  done_bar(b))
-              : "memory");
-        }
-        __syncwarp();
+        issue_l1(li);
       }
       // done: the first layer's accumulator
       if (!mbar_wait(done_bar(b), par, wl)) {
@@ -644,6 +673,16 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
               : "memory");
         }
         __syncwarp();
+        // the next tile's first layer goes to the tensor cores now, under the
+        // rest of this tile's epilogue, if that tile is filled (its
+        // accumulator, tile li - 1's, has been read back by every warp)
+        const int nx = li + 1;
+        if (nx < nlocal && mbar_test(full_bar(nx & 1), (nx >> 1) & 1) &&
+            (nx < 2 || mbar_test(empty_bar(nx & 1), ((nx >> 1) - 1) & 1))) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          issue_l1(nx);
+          early = nx;
+        }
       }
       if (!mbar_wait(out_bar(b), par, wl)) {
         ok = false;

@@ -13,6 +13,16 @@
 // Two batches can be in flight: the next one is launched while the previous
 // one still runs.  The context's error word is copied out and cleared after
 // each batch, so an out-of-range event is attributed to its own batch.
+//
+// With resident windows (window_us > 0) each sensor stream has its own
+// context (its sensor size, the server's frequencies and weights) and its
+// own sliding-window stream (veckm_stream: exact fixed-point per-pixel sums
+// of the window's events, resident on the device) and CUDA stream, created
+// with the stream's first packet.  The worker pushes each packet onto its
+// sensor's window on that sensor's CUDA stream; packets of different sensors
+// overlap on the device (up to kMaxInflightW), complete in any order and are
+// reported as they complete, while their arena regions return to the ring in
+// arrival order.  A packet's region also holds its flows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,9 +44,12 @@ using Clock = std::chrono::steady_clock;
 namespace {
 
 constexpr int kMaxInflight = 2;
+constexpr int kMaxInflightW = 64;  // resident windows: packets in flight at once
 
 int64_t al256(int64_t b) { return (b + 255) & ~int64_t(255); }
 int64_t footprint(int64_t n) { return 2 * al256(2 * n) + al256(4 * n); }
+// resident windows: the events and then the flows (8 bytes per event)
+int64_t footprint_w(int64_t n) { return footprint(n) + al256(8 * n); }
 
 struct Pkt {
   veckm_packet p{};
@@ -44,6 +57,20 @@ struct Pkt {
   cudaEvent_t uploaded = nullptr;
   bool ready = false;
   Clock::time_point t_submit;
+  // resident windows
+  uint32_t t_hi = 0;           // the packet's last (largest) time
+  int slot = 0;                // pinned error word
+  cudaEvent_t start = nullptr, done = nullptr;
+  veckm_status launch_st = VECKM_OK;
+  bool reported = false;
+};
+
+// A sensor stream's resident state (resident windows).
+struct Sensor {
+  veckm_ctx *ctx = nullptr;
+  veckm_stream *st = nullptr;
+  cudaStream_t cs = nullptr;
+  int32_t W = 0, H = 0;
 };
 
 struct Batch {
@@ -80,6 +107,14 @@ struct veckm_server {
   std::thread worker;
   std::deque<Batch> inflight;  // worker thread only
   int next_slot = 0;
+  // resident windows
+  int32_t window_us = 0;
+  int64_t window_cap = int64_t(1) << 22;
+  std::mutex sensor_mu;
+  std::vector<Sensor *> sensors;  // by stream id (created with a stream's first packet)
+  int *h_errw = nullptr;          // pinned, one per packet in flight
+  std::deque<Pkt> wf;             // worker thread only: packets in flight, launch order
+  int next_wslot = 0;
 
   // Live packets occupy [tail, head) or, once the ring has wrapped, [tail,
   // wrap_end) and [0, head); both allocation and release go in arrival order.
@@ -132,7 +167,172 @@ struct veckm_server {
   void retire(bool block);
   bool launch(std::vector<Pkt> &pk);
   void run();
+  // resident windows
+  Sensor *sensor_for(const veckm_packet *p, veckm_status *st);
+  void retire_w(bool block);
+  void launch_w(Pkt &k);
+  void run_w();
 };
+
+// The sensor state of p's stream, created with the stream's first packet
+// (caller's thread).  VECKM_EBUSY if it cannot be allocated; VECKM_EINVAL if
+// the stream's sensor size changed.
+Sensor *veckm_server::sensor_for(const veckm_packet *p, veckm_status *st) {
+  std::lock_guard<std::mutex> lk(sensor_mu);
+  Sensor *sn = sensors[p->stream_id];
+  if (sn) {
+    if (sn->W != p->width || sn->H != p->height) {
+      *st = fail_msg(VECKM_EINVAL, "stream %d changed its sensor from %dx%d to %dx%d",
+                     p->stream_id, sn->W, sn->H, p->width, p->height);
+      return nullptr;
+    }
+    *st = VECKM_OK;
+    return sn;
+  }
+  sn = new (std::nothrow) Sensor();
+  if (!sn) {
+    *st = fail_msg(VECKM_EBUSY, "host memory for a stream's state");
+    return nullptr;
+  }
+  sn->W = p->width;
+  sn->H = p->height;
+  veckm_config c{};
+  c.width = p->width;
+  c.height = p->height;
+  c.D = ctx->g.D;
+  c.dx = ctx->g.dx;
+  c.dy = ctx->g.dy;
+  c.hidden = ctx->hidden;
+  c.dt_us = ctx->dt_us;
+  c.t_span_us = ctx->t_span;
+  c.sigma2 = ctx->sigma2;
+  c.h_T = ctx->T.data();
+  c.h_X = ctx->X.data();
+  c.h_Y = ctx->Y.data();
+  c.h_W1 = ctx->hW1.data();
+  c.h_b1 = ctx->hb1.data();
+  c.h_W2 = ctx->hW2.data();
+  c.h_b2 = ctx->hb2.data();
+  c.flags = ctx->flags;
+  veckm_status s = veckm_create(&sn->ctx, &c);
+  if (s == VECKM_OK) s = veckm_stream_create(sn->ctx, window_us, window_cap, &sn->st);
+  if (s == VECKM_OK && cudaStreamCreateWithFlags(&sn->cs, cudaStreamNonBlocking) != cudaSuccess)
+    s = fail_msg(VECKM_ECUDA, "stream creation");
+  if (s == VECKM_OK) s = veckm_autotune(sn->ctx, sn->W, sn->H, sn->cs, nullptr);
+  if (s != VECKM_OK) {
+    if (sn->st) veckm_stream_destroy(sn->st);
+    if (sn->ctx) veckm_destroy(sn->ctx);
+    if (sn->cs) cudaStreamDestroy(sn->cs);
+    delete sn;
+    *st = (s == VECKM_ENOMEM) ? fail_msg(VECKM_EBUSY, "no device memory for stream %d's window",
+                                         p->stream_id)
+                              : s;
+    return nullptr;
+  }
+  sensors[p->stream_id] = sn;
+  *st = VECKM_OK;
+  return sn;
+}
+
+void veckm_server::launch_w(Pkt &k) {
+  Sensor *sn = sensors[k.p.stream_id];  // created at submission
+  cudaStream_t cs = sn->cs;
+  char *base = arena + k.off;
+  const int64_t n = k.p.n;
+  const int16_t *x = reinterpret_cast<const int16_t *>(base);
+  const int16_t *y = reinterpret_cast<const int16_t *>(base + al256(2 * n));
+  const uint32_t *t = reinterpret_cast<const uint32_t *>(base + 2 * al256(2 * n));
+  float *f = reinterpret_cast<float *>(base + footprint(n));
+  k.slot = next_wslot;
+  next_wslot = (next_wslot + 1) % kMaxInflightW;
+  cudaEventCreate(&k.start);
+  cudaEventCreate(&k.done);
+  cudaStreamWaitEvent(cs, k.uploaded, 0);
+  cudaEventRecord(k.start, cs);
+  k.launch_st = veckm_stream_push(sn->st, x, y, t, n, k.t_hi, f, 1, cs);
+  cudaMemcpyAsync(h_errw + k.slot, sn->ctx->err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  cudaMemsetAsync(sn->ctx->err, 0, sizeof(int), cs);
+  if (k.launch_st == VECKM_OK)
+    cudaMemcpyAsync(k.p.h_flow, f, (size_t)n * 8, cudaMemcpyDeviceToHost, cs);
+  cudaEventRecord(k.done, cs);
+  wf.push_back(k);
+}
+
+// Reports every finished packet (in any order) and returns the arena regions
+// at the front of the ring whose packets have been reported.
+void veckm_server::retire_w(bool block) {
+  if (block && !wf.empty()) {
+    for (Pkt &k : wf)
+      if (!k.reported) {
+        cudaEventSynchronize(k.done);
+        break;
+      }
+  }
+  const Clock::time_point now = Clock::now();
+  std::lock_guard<std::mutex> lk(mu);
+  bool any_done = false;
+  for (Pkt &k : wf) {
+    if (k.reported || cudaEventQuery(k.done) == cudaErrorNotReady) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, k.start, k.done);
+    const int w = h_errw[k.slot];
+    const veckm_status status =
+        k.launch_st != VECKM_OK ? k.launch_st
+        : (w & veckm::ERR_TIMEOUT) ? VECKM_ETIMEOUT
+        : (w & veckm::ERR_CAPACITY) ? VECKM_EBUSY
+        : (w & (veckm::ERR_EVENT_RANGE | veckm::ERR_INDEX_RANGE)) ? VECKM_ERANGE : VECKM_OK;
+    const double lat = std::chrono::duration<double, std::milli>(now - k.t_submit).count();
+    done.push_back(veckm_completion{k.p.tag, k.p.stream_id, status, k.p.n, lat, 1});
+    lat_ms.push_back(lat);
+    st.gpu_busy_s += ms * 1e-3;
+    st.batches += 1;
+    st.completed += 1;
+    st.events_completed += k.p.n;
+    t_last = now;
+    k.reported = true;
+    any_done = true;
+  }
+  while (!wf.empty() && wf.front().reported) {
+    Pkt &k = wf.front();
+    release(k);
+    ev_pool.push_back(k.uploaded);
+    cudaEventDestroy(k.start);
+    cudaEventDestroy(k.done);
+    wf.pop_front();
+  }
+  if (any_done) cv_done.notify_all();
+}
+
+void veckm_server::run_w() {
+  cudaSetDevice(device);
+  for (;;) {
+    retire_w(false);
+    Pkt k;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      const bool can_take = !pending.empty() && pending.front().ready &&
+                            (int)wf.size() < kMaxInflightW;
+      if (!can_take) {
+        if (stop && pending.empty() && wf.empty()) break;
+        if ((int)wf.size() >= kMaxInflightW) {
+          lk.unlock();
+          retire_w(true);
+          continue;
+        }
+        if (!wf.empty()) {
+          // packets on the device: poll them while waiting for new ones
+          cv_work.wait_for(lk, std::chrono::microseconds(50));
+          continue;
+        }
+        cv_work.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+      k = pending.front();
+      pending.pop_front();
+    }
+    launch_w(k);
+  }
+}
 
 void veckm_server::retire(bool block) {
   while (!inflight.empty()) {
@@ -291,7 +491,8 @@ veckm_status veckm_server_create(const veckm_server_config *cfg, veckm_server **
   if (!cfg || !out) return fail_msg(VECKM_EINVAL, "null argument");
   *out = nullptr;
   if (cfg->arena_bytes < 0 || cfg->max_batch_packets < 0 || cfg->max_batch_events < 0 ||
-      cfg->max_batch_events > VECKM_MAX_EVENTS)
+      cfg->max_batch_events > VECKM_MAX_EVENTS || cfg->window_us < 0 ||
+      cfg->window_capacity < 0 || cfg->window_capacity > VECKM_MAX_EVENTS)
     return fail_msg(VECKM_EINVAL, "bad server limits");
   veckm_server *s = new (std::nothrow) veckm_server();
   if (!s) return fail_msg(VECKM_ENOMEM, "host allocation");
@@ -328,7 +529,19 @@ veckm_status veckm_server_create(const veckm_server_config *cfg, veckm_server **
   }
   s->cap = std::max<int64_t>(arena, 256);
   s->seen_stream.assign(65536, 0);
-  s->worker = std::thread([s] { s->run(); });
+  s->window_us = cfg->window_us;
+  if (cfg->window_capacity > 0) s->window_cap = cfg->window_capacity;
+  if (s->window_us > 0) {
+    s->sensors.assign(65536, nullptr);
+    if (veckm::host_malloc(reinterpret_cast<void **>(&s->h_errw), kMaxInflightW * sizeof(int)) !=
+        cudaSuccess) {
+      veckm_server_destroy(s);
+      return fail_msg(VECKM_ENOMEM, "server error words");
+    }
+    s->worker = std::thread([s] { s->run_w(); });
+  } else {
+    s->worker = std::thread([s] { s->run(); });
+  }
   *out = s;
   return VECKM_OK;
 }
@@ -341,9 +554,23 @@ veckm_status veckm_server_submit(veckm_server *s, const veckm_packet *p) {
   if (p->width < 1 || p->height < 1 || p->width > s->ctx->g.W || p->height > s->ctx->g.H)
     return fail_msg(VECKM_EINVAL, "packet sensor %dx%d outside the %dx%d canvas", p->width,
                     p->height, s->ctx->g.W, s->ctx->g.H);
-  if (p->n > s->max_events) return fail_msg(VECKM_EINVAL, "packet larger than a batch");
+  if (s->window_us == 0 && p->n > s->max_events)
+    return fail_msg(VECKM_EINVAL, "packet larger than a batch");
+  if (s->window_us > 0 && p->n > s->window_cap)
+    return fail_msg(VECKM_EINVAL, "packet larger than a stream's window capacity");
   const Clock::time_point now = Clock::now();
-  const int64_t bytes = footprint(p->n);
+  const int64_t bytes = s->window_us > 0 ? footprint_w(p->n) : footprint(p->n);
+  if (s->window_us > 0) {
+    // the stream's resident state (created with its first packet); no room
+    // for it refuses the packet like a full arena
+    veckm_status sst;
+    if (!s->sensor_for(p, &sst)) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.submitted += 1;
+      if (sst == VECKM_EBUSY) s->st.refused += 1;
+      return sst;
+    }
+  }
   Pkt *k = nullptr;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -368,6 +595,7 @@ veckm_status veckm_server_submit(veckm_server *s, const veckm_packet *p) {
     q.bytes = bytes;
     q.uploaded = s->take_event();
     q.t_submit = now;
+    q.t_hi = p->h_t[p->n - 1];  // resident windows: packets come sorted by time
     s->pending.push_back(q);
     k = &s->pending.back();  // deque: stable while the worker skips packets not ready
   }
@@ -437,9 +665,18 @@ void veckm_server_destroy(veckm_server *s) {
   if (s->worker.joinable()) s->worker.join();
   cudaStreamSynchronize(s->up);
   cudaStreamSynchronize(s->comp);
+  for (Sensor *sn : s->sensors) {
+    if (!sn) continue;
+    cudaStreamSynchronize(sn->cs);
+    veckm_stream_destroy(sn->st);
+    veckm_destroy(sn->ctx);
+    cudaStreamDestroy(sn->cs);
+    delete sn;
+  }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   for (float *f : s->d_flow) if (f) cudaFree(f);
   if (s->h_err) cudaFreeHost(s->h_err);
+  if (s->h_errw) cudaFreeHost(s->h_errw);
   if (s->arena) cudaFree(s->arena);
   cudaStreamDestroy(s->up);
   cudaStreamDestroy(s->comp);

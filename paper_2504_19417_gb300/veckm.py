@@ -45,7 +45,8 @@ class _Config(C.Structure):
 
 class _ServerConfig(C.Structure):
     _fields_ = [("model", _Config), ("arena_bytes", C.c_int64), ("max_batch_packets", C.c_int32),
-                ("max_batch_events", C.c_int64), ("batch_window_us", C.c_int32)]
+                ("max_batch_events", C.c_int64), ("batch_window_us", C.c_int32),
+                ("window_us", C.c_int32), ("window_capacity", C.c_int64)]
 
 
 class _Packet(C.Structure):
@@ -313,11 +314,13 @@ class Server:
 
     def __init__(self, p: Params, W1, b1, W2, b2, T=None, X=None, Y=None,
                  mlp_mode: int = MLP_FP32, arena_bytes: int = 0, max_batch_packets: int = 0,
-                 max_batch_events: int = 0, batch_window_us: int = 0):
+                 max_batch_events: int = 0, batch_window_us: int = 0, window_us: int = 0,
+                 window_capacity: int = 0):
         keep = []
         cfg = _ServerConfig(model=_make_config(p, W1, b1, W2, b2, T, X, Y, mlp_mode, keep),
                             arena_bytes=arena_bytes, max_batch_packets=max_batch_packets,
-                            max_batch_events=max_batch_events, batch_window_us=batch_window_us)
+                            max_batch_events=max_batch_events, batch_window_us=batch_window_us,
+                            window_us=window_us, window_capacity=window_capacity)
         h = C.c_void_p()
         _check(lib().veckm_server_create(C.byref(cfg), C.byref(h)))
         self._h = h
@@ -335,7 +338,7 @@ class Server:
                      height, _host_ptr(out))
         st = lib().veckm_server_submit(self._h, C.byref(pk))
         if st == VECKM_EBUSY:
-            return False
+            return False  # refused: no room in the arena (or for the stream's window)
         _check(st)
         self._bufs[tag] = (x, y, t, out)
         return True

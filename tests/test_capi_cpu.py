@@ -104,3 +104,13 @@ def test_tensor_core_head_rejects_weights_beyond_fp16_range():
     assert vk.lib().veckm_create(C.byref(h), C.byref(c)) == vk.VECKM_EUNSUPPORTED
     assert not h.value
     assert b"FP16" in vk.lib().veckm_last_error()
+
+
+def test_server_rejects_bad_window_limits_on_host():
+    c, keep = _cfg()
+    for bad in (dict(window_us=-1), dict(window_capacity=-5),
+                dict(window_capacity=(1 << 30) + 1), dict(arena_bytes=-1)):
+        sc = vk._ServerConfig(model=c, **bad)
+        h = C.c_void_p()
+        assert vk.lib().veckm_server_create(C.byref(sc), C.byref(h)) == vk.VECKM_EINVAL
+        assert not h.value

@@ -100,11 +100,13 @@ def test_predict_matches_oracle(mode, W, H, n, D):
     _check_flow(flow, _oracle_emb(sl, D, 10, 10, 16_000, TXY), w, mode)
 
 
-def test_wide_window_predicts_alternate_cleared_grids():
+@pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_FP16 | vk.ACC_FP16])
+def test_wide_window_predicts_alternate_cleared_grids(mode):
     # 41 x 37 windows: the row pass reads every pixel, so the pixel sums go
     # to a grid cleared for them (by the previous call's head, else on the
-    # side stream); dense and sparse slices alternate on one context
-    mode, D, dx, dy = vk.MLP_FP16, 64, 20, 18
+    # side stream); dense and sparse slices alternate on one context.  The
+    # column pass normalises blocks of 37 outputs, more than a warp's lanes.
+    D, dx, dy = 64, 20, 18
     sls = [synth.event_slice(120, 90, n, 10_000, n_edges=5, seed=600 + i)
            for i, n in enumerate((9_000, 1_500, 9_000, 700))]
     enc, TXY, w = make(sls[0], D, dx, dy, mode=mode, t_span_us=10_000)

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2504_19417_gb300 import synth
 from paper_2504_19417_gb300 import veckm as vk
-from tests.common import FLOW_FLOOR, flow_rel_err
+from tests.common import FLOW_FLOOR, flow_rel_err, within_half_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
@@ -166,4 +166,127 @@ def test_malformed_packets_are_rejected():
     assert ei.value.status == vk.VECKM_EINVAL
     with pytest.raises(vk.VeckmError):
         srv.submit(70_000, x, y, t, sl.t_ref, 100, 100, out)  # stream id out of range
+    srv.close()
+
+
+# ------------------------------------------------------------ resident windows
+WIN = 32_000  # 2 delta_t
+SENS = [(128, 96), (97, 61), (160, 120)]
+
+
+def _sensor_stream(i, n):
+    W, H = SENS[i]
+    return synth.event_slice(W, H, n, 150_000, n_edges=4, frac_noise=0.1, seed=700 + i,
+                             t0_us=20_000_000)
+
+
+def _cut(sl, rng, mean_us=4_000):
+    """Consecutive packets of a sensor stream at random time boundaries
+    (index ranges; every packet non-empty)."""
+    out, i = [], 0
+    t = int(sl.t[0])
+    while i < sl.n:
+        t += int(rng.integers(mean_us // 3, 2 * mean_us))
+        j = int(np.searchsorted(sl.t, t, side="right"))
+        if j > i:
+            out.append((i, j))
+            i = j
+    return out
+
+
+def _window_ref(sl, i, j, TXY, w):
+    """The packet's flows against the window [t_hi - WIN, t_hi] of its stream
+    (t_hi = its last event), recomputed from scratch by the oracle."""
+    T, X, Y = TXY
+    t_hi = int(sl.t[j - 1])
+    lo = int(np.searchsorted(sl.t, t_hi - WIN, side="left"))
+    K = np.arange(i - lo, j - lo, dtype=np.int64)
+    e = oracle.encode_pooled(sl.x[lo:j], sl.y[lo:j], sl.t[lo:j], int(sl.t[lo]), sl.width,
+                             sl.height, D, 10, 10, 16_000.0, T, X, Y, K=K)[0]
+    return e, oracle.mlp(e, w.W1, w.b1, w.W2, w.b2)
+
+
+def _submit_range(srv, sid, sl, i, j, tag):
+    x = torch.from_numpy(np.ascontiguousarray(sl.x[i:j])).pin_memory()
+    y = torch.from_numpy(np.ascontiguousarray(sl.y[i:j])).pin_memory()
+    t = torch.from_numpy(np.ascontiguousarray(sl.t[i:j]).view(np.int32)).pin_memory()
+    out = torch.zeros((j - i, 2), dtype=torch.float32).pin_memory()
+    assert srv.submit(sid, x, y, t, int(sl.t[i]), sl.width, sl.height, out, tag=tag)
+    return out
+
+
+@pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_FP32])
+def test_resident_windows_alone_equal_mix_and_match_the_oracle(mode):
+    """Each stream's packets slide its resident window; a stream's flows are
+    bit-identical whether its packets run alone or interleaved with other
+    streams' packets (on the device at the same time), and match the oracle
+    recomputed on each packet's window."""
+    streams = [_sensor_stream(i, 12_000 + 4_000 * i) for i in range(3)]
+    rng = np.random.default_rng(17)
+    cuts = [_cut(sl, rng) for sl in streams]
+    kw = dict(W=512, H=512, mode=mode, window_us=WIN, window_capacity=60_000)
+    # stream 0 alone
+    srv, TXY, w = _server(**kw)
+    alone = [_submit_range(srv, 5, streams[0], i, j, tag=q) for q, (i, j) in enumerate(cuts[0])]
+    srv.drain()
+    c = _all(srv, len(alone))
+    assert all(v["status"] == vk.VECKM_OK for v in c.values())
+    srv.close()
+    # all three interleaved at random, each stream's packets in order
+    srv, _, _ = _server(**kw)
+    order = [s for s in range(3) for _ in cuts[s]]
+    rng.shuffle(order)
+    nxt = [0, 0, 0]
+    outs = {}
+    for s in order:
+        q = nxt[s]
+        nxt[s] += 1
+        i, j = cuts[s][q]
+        outs[(s, q)] = _submit_range(srv, 5 + s, streams[s], i, j, tag=1000 * s + q)
+    srv.drain()
+    c = _all(srv, len(order))
+    assert all(v["status"] == vk.VECKM_OK for v in c.values())
+    st = srv.stats()
+    assert st["completed"] == st["admitted"] == len(order) and st["streams"] == 3
+    for q in range(len(cuts[0])):
+        assert np.array_equal(outs[(0, q)].numpy(), alone[q].numpy()), q
+    for s in range(3):
+        for q in range(0, len(cuts[s]), 5):
+            i, j = cuts[s][q]
+            e, fref = _window_ref(streams[s], i, j, TXY, w)
+            f = outs[(s, q)].numpy()
+            if mode == vk.MLP_FP32:
+                assert flow_rel_err(f, fref, FLOW_FLOOR).max() <= 1e-4, (s, q)
+            else:
+                assert within_half_bound(f, fref, e, w, mode) <= 1.0, (s, q)
+    srv.close()
+
+
+def test_resident_windows_refuse_a_stream_whose_state_cannot_be_allocated():
+    sl = _sensor_stream(0, 6_000)
+    srv, TXY, w = _server(W=512, H=512, mode=vk.MLP_FP16, window_us=WIN, window_capacity=20_000)
+    cuts = _cut(sl, np.random.default_rng(4))
+    i, j = cuts[0]
+    x = torch.from_numpy(np.ascontiguousarray(sl.x[i:j])).pin_memory()
+    y = torch.from_numpy(np.ascontiguousarray(sl.y[i:j])).pin_memory()
+    t = torch.from_numpy(np.ascontiguousarray(sl.t[i:j]).view(np.int32)).pin_memory()
+    out = torch.zeros((j - i, 2), dtype=torch.float32).pin_memory()
+    vk.debug_fail_alloc(3)  # the new stream's context fails to allocate
+    try:
+        assert not srv.submit(1, x, y, t, int(sl.t[i]), sl.width, sl.height, out)
+    finally:
+        vk.debug_fail_alloc(-1)
+    # the next packet of the stream creates its state and is served
+    assert srv.submit(1, x, y, t, int(sl.t[i]), sl.width, sl.height, out)
+    srv.drain()
+    c = _all(srv, 1)
+    assert list(c.values())[0]["status"] == vk.VECKM_OK
+    e, fref = _window_ref(sl, i, j, TXY, w)
+    assert within_half_bound(out.numpy(), fref, e, w, vk.MLP_FP16) <= 1.0
+    st = srv.stats()
+    assert st["refused"] == 1 and st["admitted"] == 1
+    # a stream may not change its sensor
+    with pytest.raises(vk.VeckmError) as ei:
+        srv.submit(1, x, y, t, int(sl.t[i]), 64, 48, out)
+    assert ei.value.status == vk.VECKM_EINVAL
     srv.close()
