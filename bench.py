@@ -821,11 +821,15 @@ def batch_leg(args, mode, stream):
     N = sum(s.n for s in sls)
     cw_max = 8192
     _, _, cw, ch = vk.canvas_layout([s.width for s in sls], [s.height for s in sls], 10, 10, cw_max)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     big = ctx(cw_max, ch)
     flow = torch.empty((N, 2), dtype=torch.float32, device="cuda")
     t0 = time.perf_counter()
     plan = big.plan(dev, out=flow)
     plan_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    batch_bytes = free0 - torch.cuda.mem_get_info()[0]
 
     def timed(fn, k):
         for _ in range(args.warmup):
@@ -842,6 +846,8 @@ def batch_leg(args, mode, stream):
 
     k = max(3, args.steps // 2)
     ms_graph = timed(lambda: plan.launch(stream), k)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
     ctxs = {}
     for s in sls:
         if (s.width, s.height) not in ctxs:
@@ -849,6 +855,8 @@ def batch_leg(args, mode, stream):
             c.autotune(s.width, s.height, stream)
             ctxs[(s.width, s.height)] = c
     outs = [torch.empty((s.n, 2), dtype=torch.float32, device="cuda") for s in sls]
+    torch.cuda.synchronize()
+    plain_bytes = free1 - torch.cuda.mem_get_info()[0]
 
     def plain():
         launches = 0
@@ -878,6 +886,9 @@ def batch_leg(args, mode, stream):
                   "form": "one veckm_predict per slice, per-resolution contexts, one stream"},
         "speedup_vs_plain": ms_plain / ms_graph, "max_rel_diff_vs_plain": agree,
         "plan_create_s": plan_s, "generate_s": gen_s,
+        "device_bytes": int(batch_bytes), "device_bytes_plain": int(plain_bytes),
+        "device_bytes_note": "free-memory drop: canvas context + plan + flows (batch); "
+                             "per-resolution contexts + flows (plain), the slices' events excluded",
         "tuned_pooling": "per geometry (autotuner), both sides"}
     plan.close()
     del big, ctxs

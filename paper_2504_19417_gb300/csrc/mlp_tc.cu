@@ -29,9 +29,10 @@
 //     outputs into columns 64..79 of the accumulator, which the epilogue
 //     reads back (tcgen05.ld), adds b2 to, and stores.
 // Shared tiles and accumulators are double buffered; the hand-offs are
-// mbarriers (full: producers -> epilogue/MMA; mma_done: MMA -> epilogue;
+// mbarriers (full: producers -> MMA; mma_done: MMA -> epilogue and
+// producers, whose operand tile is free once the first layer has run;
 // stored: epilogue -> second-layer MMA; out_done: second-layer MMA ->
-// epilogue; tmem_empty: epilogue -> MMA and producers).  No waiter can fall
+// epilogue; tmem_empty: epilogue -> MMA).  No waiter can fall
 // two phases behind a barrier (each role's next use of a buffer waits for the
 // other roles' previous use), so parity waits are unambiguous.  Every wait is
 // bounded: on time-out the kernel sets the error word and leaves.
@@ -45,9 +46,8 @@
 // producers' loads and tile stores and the MMAs' operand reads share.
 //
 // Requested events come either in pixel-sorted order (records of the
-// counting sort: consecutive rows mostly share a pooled row; producers
-// prefetch the following tile into L2) or by index (an explicit K list, or
-// all events in input order).
+// counting sort: consecutive rows mostly share a pooled row) or by index (an
+// explicit K list, or all events in input order).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -271,10 +271,12 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
   uint8_t *sA = smem;                            // 2 x [128 x IN] half, SW128
   uint8_t *sB = smem + 2 * TILE_BYTES;           // [128 x IN] half (W1), SW128
   uint8_t *sW2 = sB + TILE_BYTES;                // [16 x 128] FP16 (W2 padded), SW128
-  float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);    // [2][128] 1 / window count
-  int *sK = reinterpret_cast<int *>(sInv + 2 * kM);            // [2][128] output row codes
+  // row metadata of tile li in slot li & 3: a slot is rewritten only once the
+  // tile four back has been read back in full
+  float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);    // [4][128] 1 valid, 0 not
+  int *sK = reinterpret_cast<int *>(sInv + 4 * kM);            // [4][128] output row codes
   // full[2], done[2], empty[2], stored[2], out_done[2]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 2 * kM);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sK + 4 * kM);
   int *sMeta = reinterpret_cast<int *>(bars + 10);  // per producer warp [2][pixels R | t R]
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sMeta + kProdWarps * 4 * kRowsPerWarp);
 
@@ -481,13 +483,6 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     };
     int c_outk = -1;
     float c_inv = 0.f;
-    // pixels of this lane's row in the tile two ahead of the current one,
-    // whose pooled rows are prefetched into L2 (sorted path only)
-    int pf_pix = -1;
-    auto pf_load = [&](int t) {
-      const int i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
-      pf_pix = (rec && i < ns) ? __ldg(rpix + i) : -1;
-    };
     if (nlocal > 0) {
       int pix;
       uint32_t trel;
@@ -495,7 +490,6 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       ms_put(0, pix, trel);
       __syncwarp();
       issue(0, 0, qa);
-      pf_load((int)(blockIdx.x + 2 * gridDim.x));
     }
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
@@ -506,16 +500,8 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       float n_inv = 0.f;
       int n_outk = -1;
       if (has_next) meta(tile + (int)gridDim.x, n_pix, n_trel, n_inv, n_outk);
-      if (pf_pix >= 0) {  // L2 prefetch of this lane's half row of the tile after next
-        constexpr int kRowBytes = (HALF ? 8 : 16) * U;  // pooled bytes per pixel
-        constexpr int kHalfLines = kRowBytes / 256;      // 128-byte lines per half row
-        const char *row = reinterpret_cast<const char *>(pooled_v) + (size_t)pf_pix * kRowBytes;
-#pragma unroll
-        for (int l = 0; l < kHalfLines; ++l)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ((lane >> 4) * kHalfLines + l) * 128));
-      }
-      pf_load(tile + 3 * (int)gridDim.x);
-      if (li >= 2 && !mbar_wait(empty_bar(b), ((li >> 1) - 1) & 1, wl)) {
+      // operand tile b is free once the first layer of tile li - 2 has run
+      if (li >= 2 && !mbar_wait(done_bar(b), ((li >> 1) - 1) & 1, wl)) {
         ok = false;
         break;
       }
@@ -534,10 +520,10 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         if (h & 1) compute(b, h * kB, qb, Abuf);
         else compute(b, h * kB, qa, Abuf);
       }
-      // the epilogue reads these after the full barrier
+      // the epilogue reads these after the first layer's done barrier
       if (lane < kRowsPerWarp) {
-        sK[b * kM + pw * kRowsPerWarp + lane] = c_outk;
-        sInv[b * kM + pw * kRowsPerWarp + lane] = c_inv;
+        sK[(li & 3) * kM + pw * kRowsPerWarp + lane] = c_outk;
+        sInv[(li & 3) * kM + pw * kRowsPerWarp + lane] = c_inv;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
@@ -600,8 +586,12 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     for (int li = 0; li < nlocal && ok; ++li) {
       const int b = li & 1;
       const uint32_t par = (li >> 1) & 1;
-      // full: the producers' tile and row metadata
-      if (!mbar_wait(full_bar(b), par, wl)) {
+      // the issuing warp waits for the producers' tile (full), every epilogue
+      // warp for the first layer (done, which follows full): the producers
+      // may fill tile li + 2 once tile li's first layer has run, so full can
+      // move on before a slow epilogue warp looks at it, done cannot (tile
+      // li + 2's first layer waits for every warp's read of tile li)
+      if (warp == kMmaWarp && early != li && !mbar_wait(full_bar(b), par, wl)) {
         ok = false;
         break;
       }
@@ -620,8 +610,8 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const float inv = sInv[b * kM + row];
-      const int k = sK[b * kM + row];
+      const float inv = sInv[(li & 3) * kM + row];
+      const int k = sK[(li & 3) * kM + row];
       const float2 inv2 = make_float2(inv, inv);
       const uint32_t acc_t = tmem + lane_base + (uint32_t)(b * kN);
       // ReLU(h / n + b1) as FP16 pairs into columns [0, kN/2): chunk c reads
@@ -735,8 +725,8 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
-  const size_t sm = (size_t)3 * kM * IN * 2 + kW2Bytes + sizeof(float) * (2 * kM) +
-                    sizeof(int) * 2 * kM + 8 * 10 + sizeof(int2) * 2 * kM +
+  const size_t sm = (size_t)3 * kM * IN * 2 + kW2Bytes + sizeof(float) * (4 * kM) +
+                    sizeof(int) * 4 * kM + 8 * 10 + sizeof(int2) * 2 * kM +
                     16 + 1024;  // + SW128 alignment slack
   auto kern = k_predict_tc<DV, HALF, F16>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
