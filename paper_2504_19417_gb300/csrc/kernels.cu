@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
           for (int v = 0; v < DV; ++v) s[v] = f4zero();
         }
 #pragma unroll
-        for (int v = 0; v < DV; ++v) s[v] = add4x2(s[v], time_phase2_lean(tj, w[v][0], w[v][1]));
+        for (int v = 0; v < DV; ++v) s[v] = add4x2(s[v], time_phase2_packed(tj, w[v][0], w[v][1]));
       }
     }
     // the last range's last pixel, when it started inside the range, has no
@@ -708,13 +708,13 @@ enum class Pass { Rows, Cols };
 // EMIT (column pass only) picks the output form: kEmitF32, the window sums
 // as they are; kEmitF16N, divided by the pixel's window count n (Eq. 17; 0
 // where the window is empty) and stored as FP16, unit u of a pixel = 8 bytes
-// (Re 2u, Re 2u+1, Im 2u, Im 2u+1); kEmitF32N, divided by n and stored as
-// FP32 in the order (Re 2u, Re 2u+1, Im 2u, Im 2u+1), so that the real and the
-// imaginary parts of a unit are register pairs for packed FP32x2 arithmetic.
+// (Re 2u, Re 2u+1, Im 2u, Im 2u+1); kEmitF32P, the window sums as FP32 in the
+// order (Re 2u, Re 2u+1, Im 2u, Im 2u+1), so that the real and the imaginary
+// parts of a unit are register pairs for packed FP32x2 arithmetic.
 // occ (row pass, window length L <= 32): per-pixel event counts; pixels with
 // none are taken as zero without reading src, whose rows there may hold
 // anything.
-enum : int { kEmitF32 = 0, kEmitF16N = 1, kEmitF32N = 2 };
+enum : int { kEmitF32 = 0, kEmitF16N = 1, kEmitF32P = 2 };
 template <int DV, Pass P, int EMIT = kEmitF32>
 __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
                                                  const int *__restrict__ occ = nullptr) {
   static_assert(EMIT == kEmitF32 || P == Pass::Cols, "normalised output: column pass only");
   constexpr bool HALF = EMIT == kEmitF16N;
-  constexpr bool NORM = EMIT != kEmitF32;  // divided by the window counts
+  constexpr bool NORM = HALF;  // divided by the window counts
   constexpr int U = 32 * DV;
   extern __shared__ float4 smem[];
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
@@ -888,9 +888,8 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
           reinterpret_cast<uint2 *>(dst)[base + (size_t)pos * stride + u] =
               make_uint2(*reinterpret_cast<const uint32_t *>(&re),
                          *reinterpret_cast<const uint32_t *>(&im));
-        } else if (EMIT == kEmitF32N) {
-          dst[base + (size_t)pos * stride + u] =
-              make_float4(o.x * inv, o.z * inv, o.y * inv, o.w * inv);
+        } else if (EMIT == kEmitF32P) {
+          dst[base + (size_t)pos * stride + u] = make_float4(o.x, o.z, o.y, o.w);
         } else {
           dst[base + (size_t)pos * stride + u] = o;
         }
@@ -1634,9 +1633,9 @@ int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbu
                                                               s, ncnt, tn.cols_seg, tn.cols_wpb)));
 }
 
-int launch_pool_cols_norm(const Geometry &g, const Tables &tb, const float4 *hbuf,
-                          const int *ncnt, float4 *pooled, cudaStream_t s, const Tune &tn) {
-  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, kEmitF32N>(g, tb, hbuf, pooled, s, ncnt,
+int launch_pool_cols_pair(const Geometry &g, const Tables &tb, const float4 *hbuf,
+                          float4 *pooled, cudaStream_t s, const Tune &tn) {
+  VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Cols, kEmitF32P>(g, tb, hbuf, pooled, s, nullptr,
                                                               tn.cols_seg, tn.cols_wpb)));
 }
 

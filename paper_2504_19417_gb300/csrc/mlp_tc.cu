@@ -354,12 +354,12 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
               (u & 1) * 8;
     }
     // Row metadata of tile t for lane j < 16 (row pw*16 + j): the pixel whose
-    // pooled vector is read, t - t_ref, 1 for a valid event (0 otherwise;
-    // the pooled grid is already divided by the window counts) and the output
-    // row (-1: none; invalid_row(i): an invalid event whose flow is written as
-    // zeros).  Rows past the end and invalid events read pixel 0: the MMA
-    // keeps rows apart and their results are discarded.  Every load here is
-    // consumed a tile later, so the warp never waits on it.
+    // pooled vector is read, t - t_ref, 1 for a valid event (0 otherwise; the
+    // FP32-grid path later replaces it by 1/n) and the output row (-1: none;
+    // invalid_row(i): an invalid event whose flow is written as zeros).  Rows
+    // past the end and invalid events read pixel 0: the MMA keeps rows apart
+    // and their results are discarded.  Every load here is consumed a tile
+    // later, so the warp never waits on it.
     auto meta = [&](int t, int &pix, uint32_t &trel, float &inv, int &outk) {
       const int i = t * kM + pw * kRowsPerWarp + (lane & (kRowsPerWarp - 1));
       pix = 0;
@@ -407,9 +407,10 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       }
     };
     const uint32_t sA_a = smem_u32(sA);
-    // both grids are already divided by n; FP16 grid: uint2 (half2 Re pair,
-    // half2 Im pair) per unit; FP32 grid: float4 (re 2u, re 2u+1, im 2u,
-    // im 2u+1), the real and imaginary pairs of packed FP32x2 arithmetic
+    // FP16 grid: uint2 (half2 Re pair, half2 Im pair) per unit, already
+    // divided by n; FP32 grid: float4 (re 2u, re 2u+1, im 2u, im 2u+1), the
+    // real and imaginary pairs of packed FP32x2 arithmetic (the epilogue
+    // divides by n: the first layer is linear)
     using Q = typename std::conditional<HALF, uint2, float4>::type;
     const Q *pooled = reinterpret_cast<const Q *>(pooled_v);
     // rows per batch: the loads of one batch are in flight while the previous
@@ -483,10 +484,12 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     };
     int c_outk = -1;
     float c_inv = 0.f;
+    int n_cnt = 0;  // FP32 grid: window count of this lane's row in the next tile
     if (nlocal > 0) {
       int pix;
       uint32_t trel;
       meta(blockIdx.x, pix, trel, c_inv, c_outk);
+      if (!HALF && c_inv != 0.f) c_inv = 1.0f / (float)__ldg(ncnt + pix);
       ms_put(0, pix, trel);
       __syncwarp();
       issue(0, 0, qa);
@@ -519,6 +522,9 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
         }
         if (h & 1) compute(b, h * kB, qb, Abuf);
         else compute(b, h * kB, qa, Abuf);
+        // FP32 grid: the window count of the next tile's row, loaded mid-tile
+        // (its pixel has arrived by then) and inverted at the tile's end
+        if (!HALF && h == NB / 2 - 1 && has_next && n_inv != 0.f) n_cnt = __ldg(ncnt + n_pix);
       }
       // the epilogue reads these after the first layer's done barrier
       if (lane < kRowsPerWarp) {
@@ -530,7 +536,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
       // (the stall injection of the error-path tests withholds this signal)
       if (lane == 0 && !mlp.inject_stall) mbar_arrive(full_bar(b));
       c_outk = n_outk;
-      c_inv = n_inv;
+      c_inv = (!HALF && n_inv != 0.f) ? 1.0f / (float)n_cnt : n_inv;
     }
   } else {
     // ------------------------------------------------------------ epilogue

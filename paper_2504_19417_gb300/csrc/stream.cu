@@ -473,7 +473,7 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   const bool tc_head = predict && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16));
   const bool half_grid = tc_head && (c->flags & VECKM_ACC_FP16);
   r = half_grid ? launch_pool_cols_half(g, tb, c->hbuf, c->ncnt, c->acc, cs, tn)
-      : tc_head ? launch_pool_cols_norm(g, tb, c->hbuf, c->ncnt, c->acc, cs, tn)
+      : tc_head ? launch_pool_cols_pair(g, tb, c->hbuf, c->acc, cs, tn)
                 : launch_pool_cols(g, tb, c->hbuf, c->acc, cs, tn);
   if (r < 0) return fail_cuda(cudaGetLastError(), "pooling (columns) launch");
   launches += r;

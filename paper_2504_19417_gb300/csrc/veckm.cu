@@ -392,15 +392,15 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   mark();
   join.wait();  // the window counts (side stream)
   mark();
-  // The tensor-core head reads the pooled grid already divided by the window
-  // counts: FP16 (VECKM_ACC_FP16), else FP32 with each unit's real and
-  // imaginary parts paired; the other consumers read the plain window sums.
+  // The tensor-core head reads the pooled grid as FP16 divided by the window
+  // counts (VECKM_ACC_FP16), else as FP32 window sums with each unit's real
+  // and imaginary parts paired; the other consumers read the plain sums.
   const bool tc_head = what == Out::Flow && (c->flags & (VECKM_MLP_BF16 | VECKM_MLP_FP16));
   const bool half_grid = tc_head && (c->flags & VECKM_ACC_FP16);
   if (half_grid)
     r = launch_pool_cols_half(g, tb, grow, c->ncnt, gsum, s, tn);
   else if (tc_head)
-    r = launch_pool_cols_norm(g, tb, grow, c->ncnt, gsum, s, tn);
+    r = launch_pool_cols_pair(g, tb, grow, gsum, s, tn);
   else
     r = launch_pool_cols(g, tb, grow, gsum, s, tn);
   if (r < 0) return cuda_fail(cudaGetLastError(), "pooling (columns) launch");

@@ -46,8 +46,8 @@ struct MLP {
   const uint16_t *W1h;   // [hidden][2D] BF16 or FP16 bits, core-matrix order for tcgen05
   int hidden;
   int half_kind;         // 0: BF16, 1: FP16 (for W1h)
-  int pooled_half;       // tensor-core head: 1, the pooled grid is FP16 (else FP32 in the
-                         // launch_pool_cols_norm order); either way divided by the counts
+  int pooled_half;       // tensor-core head: 1, the pooled grid is FP16 and divided by the
+                         // counts; 0, FP32 window sums in the launch_pool_cols_pair order
   // host copies of b1, W2, b2 (kernel parameters of the tensor-core head)
   const float *hb1 = nullptr, *hW2 = nullptr, *hb2 = nullptr;
   // [16][hidden] FP16 bits: W2 padded to 16 rows, core-matrix order for
@@ -116,11 +116,11 @@ int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cu
 // per pixel D/2 units of 8 bytes (Re 2u, Re 2u+1, Im 2u, Im 2u+1).
 int launch_pool_cols_half(const Geometry &g, const Tables &tb, const float4 *hbuf,
                           const int *ncnt, void *pooled16, cudaStream_t s, const Tune &tn = Tune{});
-// Column pass writing the pooled grid divided by the window counts as FP32,
-// unit u of a pixel = (Re 2u, Re 2u+1, Im 2u, Im 2u+1): the grid the
-// tensor-core head reads when the pooled grid is kept in FP32.
-int launch_pool_cols_norm(const Geometry &g, const Tables &tb, const float4 *hbuf,
-                          const int *ncnt, float4 *pooled, cudaStream_t s, const Tune &tn = Tune{});
+// Column pass writing the pooled grid (the window sums) as FP32 with unit u
+// of a pixel = (Re 2u, Re 2u+1, Im 2u, Im 2u+1): the grid the tensor-core head
+// reads when the pooled grid is kept in FP32.
+int launch_pool_cols_pair(const Geometry &g, const Tables &tb, const float4 *hbuf,
+                          float4 *pooled, cudaStream_t s, const Tune &tn = Tune{});
 int launch_gather_emb(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                       const Tables &tb, const float4 *pooled, const int *ncnt, float *emb,
                       int *err, cudaStream_t s);
