@@ -1,49 +1,48 @@
 // Perceptron on the 5th-generation tensor cores, fused with the gather.
 //
-// Warp-specialised pipeline, each CTA with two 128-event tiles in flight
-// (D = 64: two CTAs per SM with 8 producer warps each; D = 128: one CTA
-// per SM, whose operand tiles fill shared memory, with 16 producer warps):
+// Each 128-event tile takes the first layer (Eq. 6) as one 128 x 128 x 2D
+// tcgen05.mma chain (K steps of 16, FP32 accumulator in tensor memory) and
+// the second layer as one 128 x 16 x 128 chain.  Warp-specialised roles:
 //   - producer warps gather the rows of a tile, P[p] * conj(exp(i t T/dt))
 //     (the pooled value at the event's pixel times the conjugate temporal
-//     phase, Eq. 16), straight into shared memory as BF16 (or FP16) in the
-//     K-major 128-byte-swizzled layout that tcgen05.mma reads: the tile is
-//     split into K-blocks of 64 columns; in K-block kb, row m occupies the
-//     128 bytes at kb * (128 rows * 128 B) + (m / 8) * 1024 + (m % 8) * 128,
-//     and its 16-byte chunk c sits at chunk position c XOR (m % 8), so a warp
-//     writing one row covers 32 distinct banks.  The K axis is ordered per
-//     unit u as Re(2u), Re(2u+1), Im(2u), Im(2u+1) (one 8-byte store per lane
-//     and row); W1 is stored the same way with its columns permuted to match.
-//     Each warp keeps one batch of pooled-row loads in flight while it
-//     computes the previous batch, across tile boundaries.
-//   - 4 epilogue warps; the first also issues the tile's 2D/16 MMAs of shape
-//     128 x 128 x 16 into one of two FP32 accumulators in tensor memory
-//     (2 x 128 columns) and commits them to an mbarrier.  The epilogue reads
-//     the accumulator back with tcgen05.ld (warp w owns TMEM lanes
-//     32w..32w+31, one event row per thread), applies the window count
+//     phase, Eq. 16), rounded to BF16 (or FP16), the first layer's A operand.
+//     The K axis is ordered per unit u as Re(2u), Re(2u+1), Im(2u), Im(2u+1);
+//     W1 is stored with its columns permuted to match.
+//   - epilogue warps read the accumulator back with tcgen05.ld (TMEM lane =
+//     tile row, one event row per thread), apply the window-count
 //     normalisation and b1 in one FMA (the first layer is linear, so
-//     W1 (x / n) = (W1 x) / n), and writes ReLU(h) as FP16 pairs back into
+//     W1 (x / n) = (W1 x) / n), and write ReLU(h) as FP16 pairs back into
 //     the first 64 columns of the same accumulator (tcgen05.st).  The second
-//     layer then runs on the tensor cores too: one 128 x 16 x 128 MMA chain
-//     (K steps of 16) with A = ReLU(h) read from tensor memory and B = W2
-//     (2 x 128, padded to 16 rows, FP16 in shared memory) writes the two
-//     outputs into columns 64..79 of the accumulator, which the epilogue
-//     reads back (tcgen05.ld), adds b2 to, and stores.
-// Shared tiles and accumulators are double buffered; the hand-offs are
-// mbarriers (full: producers -> MMA; mma_done: MMA -> epilogue and
-// producers, whose operand tile is free once the first layer has run;
-// stored: epilogue -> second-layer MMA; out_done: second-layer MMA ->
-// epilogue; tmem_empty: epilogue -> MMA).  No waiter can fall
-// two phases behind a barrier (each role's next use of a buffer waits for the
-// other roles' previous use), so parity waits are unambiguous.  Every wait is
-// bounded: on time-out the kernel sets the error word and leaves.
+//     layer reads that A operand from tensor memory and B = W2 (2 x 128,
+//     padded to 16 rows, FP16 in shared memory) and writes the two outputs
+//     into columns 64..79 of the accumulator, which the epilogue reads back
+//     (tcgen05.ld), adds b2 to, and stores.  One thread of an epilogue warp
+//     issues the MMAs and commits them to mbarriers.
+// Two kernels:
+//   - k_predict_tm (D = 64): the producers write the A operand straight into
+//     tensor memory (tcgen05.st, one event row per thread), four tiles in
+//     production at once (four A slots of 64 columns) and two epilogue groups
+//     with an accumulator each (2 x 128 columns): 24 warps, one CTA per SM.
+//   - k_predict_tc (D = 128, whose A operand would not leave room for two
+//     accumulators in tensor memory): the producers write the A operand into
+//     shared memory in the K-major 128-byte-swizzled layout tcgen05.mma
+//     reads; two tiles in flight; one epilogue group that issues the next
+//     tile's first layer under the current tile's epilogue.
+// The hand-offs are mbarriers (full: producers -> MMA; done: first layer ->
+// epilogue and producers, whose operand slot is free once the first layer has
+// run; stored: epilogue -> second-layer MMA; out: second-layer MMA ->
+// epilogue; empty: epilogue -> next first layer into the same accumulator).
+// No waiter can fall two phases behind a barrier (each role's next use of a
+// buffer waits for the other roles' previous use), so parity waits are
+// unambiguous.  Every wait is bounded: on time-out the kernel sets the error
+// word and leaves.
 //
 // While they wait for accumulators, the epilogue warps can also zero a grid
 // buffer for the caller (the next call's per-pixel sums): each CTA clears one
 // contiguous share, a slice per tile, and on an early exit the rest of it.
 //
 // b1 and b2 reach the epilogue as a kernel parameter: read through the
-// constant cache, they take no slots of the shared-memory pipe, which the
-// producers' loads and tile stores and the MMAs' operand reads share.
+// constant cache, they take no slots of the shared-memory pipe.
 //
 // Requested events come either in pixel-sorted order (records of the
 // counting sort: consecutive rows mostly share a pooled row) or by index (an
@@ -65,12 +64,12 @@ namespace {
 constexpr int kM = 128;  // events per tile (MMA M)
 constexpr int kN = 128;  // hidden units (MMA N)
 constexpr int kEpiWarps = 4;
-// Producer warps: 8 of 16 rows each for D = 64 (two CTAs of 12 warps per SM);
-// 16 of 8 rows each for D = 128, whose operand tiles allow one CTA per SM
-// (20 warps then keep the loads of more rows in flight)
+// k_predict_tc: 16 producer warps of 8 rows each (one CTA per SM: the
+// operand tiles fill shared memory)
 template <int DV>
 struct Shape {
-  static constexpr int prod = DV == 1 ? 8 : 16;
+  static_assert(DV == 2, "k_predict_tc serves D = 128");
+  static constexpr int prod = 16;
   static constexpr int rows = 128 / prod;
   static constexpr int threads = 32 * (4 + prod);
 };
@@ -254,7 +253,7 @@ __device__ __forceinline__ void lds_ints(const int *p, int (&o)[N]) {
 
 // F16: the operands are FP16 (else BF16), fixed per launch.
 template <int DV, bool HALF, bool F16>
-__global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
+__global__ void __launch_bounds__(Shape<DV>::threads, 1)
     k_predict_tc(Events ev, const int64_t *__restrict__ K, int64_t nK,
                  const int2 *__restrict__ rec, const int *__restrict__ rpix,
                  const int *__restrict__ nsorted, Geometry g, Tables tb,
@@ -328,9 +327,8 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
 
   if (warp >= kEpiWarps) {
     // ------------------------------------------------------------ producers
-    // Warp pw fills rows pw*R .. pw*R+R-1 of every tile (R = kRowsPerWarp,
-    // 16 or 8).  Lane l computes
-    // unit u = l + 32 v (channels 2u, 2u+1) of a row and stores its four
+    // Warp pw fills rows pw*R .. pw*R+R-1 of every tile (R = kRowsPerWarp =
+    // 8).  Lane l computes unit u = l + 32 v (channels 2u, 2u+1) of a row and stores its four
     // halves, Re(2u) Re(2u+1) Im(2u) Im(2u+1), as one 8-byte group at K
     // positions 4u..4u+3 (W1's columns are permuted to match on the host).
     const int pw = warp - kEpiWarps;
@@ -398,7 +396,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, DV == 1 ? 2 : 1)
     // pixels and t - t_ref of this warp's rows, two tiles: [tile parity]
     // [pixel of rows 0..R-1 | t of rows 0..R-1], so that a batch's pixels (or
     // times) come in one or two vector loads (16-byte aligned: the region
-    // starts 16-byte aligned and R is 8 or 16)
+    // starts 16-byte aligned and R is 8)
     int *ms = sMeta + pw * 4 * kRowsPerWarp;
     auto ms_put = [&](int par, int pix, uint32_t trel) {
       if (lane < kRowsPerWarp) {
@@ -726,8 +724,7 @@ template <int DV, bool HALF, bool F16>
 int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                     const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                     const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
-                    cudaStream_t s, int ctas_req, float4 *zero_buf, int64_t zero_units,
-                    bool *zeroed) {
+                    cudaStream_t s, float4 *zero_buf, int64_t zero_units, bool *zeroed) {
   if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
@@ -741,8 +738,7 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return -1;
   constexpr int kThreads = Shape<DV>::threads;
-  int per_sm = std::min(blocks_per_sm((const void *)kern, kThreads, sm), 512 / kTmemCols);
-  if (ctas_req > 0) per_sm = std::min(per_sm, ctas_req);
+  const int per_sm = std::min(blocks_per_sm((const void *)kern, kThreads, sm), 512 / kTmemCols);
   const int64_t tiles = (nK + kM - 1) / kM;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm);
   // zero the buffer only when every CTA has tiles enough to spread its share
@@ -762,6 +758,433 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   return 1;
 }
 
+// ---------------------------------------------------------------------------
+// D = 64: the first layer's A operand written straight into tensor memory.
+//
+// One CTA per SM of 24 warps: 16 producer warps in four groups of 4, one
+// event row per thread, and 8 epilogue warps in two groups of 4.  A producer
+// thread forms its row's 128 K-values (P[p] conj(exp(i t T/dt)) in the
+// (Re 2u, Re 2u+1, Im 2u, Im 2u+1) order of W1's permuted columns) in chunks
+// of 4 units and writes them as FP16 (or BF16) pairs into the tile's A slot
+// of tensor memory (tcgen05.st, the warp's 32 lanes = its 32 rows).  Tensor
+// memory: four A slots of 64 columns (tile li in slot li mod 4, filled by
+// producer group li mod 4) and two accumulators of 128 columns (tile li in
+// accumulator li mod 2, read back by epilogue group li mod 2, whose first
+// warp issues the tile's MMAs).  The first layer reads A from tensor memory
+// and W1 from shared memory; the epilogue and the second layer are as in
+// k_predict_tc.  No operand tile takes shared memory, so four tiles can be in
+// production at once and a producer group waits only for its own previous
+// tile's first layer.
+constexpr int kTmProdGroups = 4;
+constexpr int kTmEpiGroups = 2;
+constexpr int kTmThreads = 32 * 4 * (kTmProdGroups + kTmEpiGroups);
+constexpr int kTmACols = 64;   // A slot: 128 K values as FP16 pairs
+constexpr int kTmAccBase = kTmProdGroups * kTmACols;  // accumulators after the A slots
+constexpr int kTmCols = 512;
+constexpr int kTmMeta = 8;     // row-metadata slots (tile li in li mod 8)
+
+template <bool HALF, bool F16>
+__global__ void __launch_bounds__(kTmThreads, 1)
+    k_predict_tm(Events ev, const int64_t *__restrict__ K, int64_t nK,
+                 const int2 *__restrict__ rec, const int *__restrict__ rpix,
+                 const int *__restrict__ nsorted, Geometry g, Tables tb,
+                 const void *__restrict__ pooled_v, const int *__restrict__ ncnt, MLP mlp,
+                 float *__restrict__ flow, int *err, float4 *__restrict__ zero_buf,
+                 int64_t zero_units, const __grid_constant__ EpiParams ep) {
+  constexpr int U = 32;        // units per pixel (D = 64)
+  constexpr int IN = 4 * U;    // 2D, the MMA K extent
+  constexpr int W1_BYTES = kN * IN * 2;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sB = smem;                       // [128 x IN] half (W1), SW128
+  uint8_t *sW2 = sB + W1_BYTES;             // [16 x 128] FP16 (W2 padded), SW128
+  float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);  // [kTmMeta][128] 1/n (or 1), 0 invalid
+  int *sK = reinterpret_cast<int *>(sInv + kTmMeta * kM);    // [kTmMeta][128] output row codes
+  uint4 *sWt = reinterpret_cast<uint4 *>(sK + kTmMeta * kM); // [32] frequencies of channels 2u, 2u+1
+  // full[4], done[4], stored[2], out[2], empty[2], drain[2]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sWt + U);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 16);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int fp16 = F16 ? 1 : 0;
+  const long long wl = mlp.wait_cycles;
+  {  // W1, W2 (already in SW128 order) and the temporal frequencies
+    const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
+    uint4 *dst = reinterpret_cast<uint4 *>(sB);
+    for (int i = tid; i < W1_BYTES / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    const uint4 *src2 = reinterpret_cast<const uint4 *>(mlp.W2h);
+    uint4 *dst2 = reinterpret_cast<uint4 *>(sW2);
+    for (int i = tid; i < kW2Bytes / 16; i += blockDim.x) dst2[i] = __ldg(src2 + i);
+    if (tid < U) sWt[tid] = __ldg(reinterpret_cast<const uint4 *>(tb.wt) + tid);
+  }
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto done_bar = [&](int s) { return bar0 + 8u * (4 + s); };
+  auto stored_bar = [&](int g) { return bar0 + 8u * (8 + g); };
+  auto out_bar = [&](int g) { return bar0 + 8u * (10 + g); };
+  auto empty_bar = [&](int g) { return bar0 + 8u * (12 + g); };
+  auto drain_bar = [&](int g) { return bar0 + 8u * (14 + g); };
+  if (tid == 0) {
+    for (int s = 0; s < 4; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(full_bar(s)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_bar(s)));
+    }
+    for (int g2 = 0; g2 < 2; ++g2) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(stored_bar(g2)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(out_bar(g2)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(empty_bar(g2)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(drain_bar(g2)));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(kTmCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int ns = rec ? *nsorted : (int)nK;
+  const int ntiles_all = (int)((nK + kM - 1) / kM);
+  const int nlocal = (int)blockIdx.x < ntiles_all
+                         ? (ntiles_all - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                         : 0;
+  bool ok = true;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // this warp's TMEM lanes
+  const int row = (warp & 3) * 32 + lane;                        // = tile row
+
+  if (warp >= 4 * kTmEpiGroups) {
+    // ------------------------------------------------------------ producers
+    const int pg = (warp - 4 * kTmEpiGroups) >> 2;  // tiles li = pg mod 4, A slot pg
+    using Q = typename std::conditional<HALF, uint2, float4>::type;
+    const Q *pooled = reinterpret_cast<const Q *>(pooled_v);
+    const uint32_t a_t = tmem + lane_base + (uint32_t)(pg * kTmACols);
+    // Row metadata of local tile li: the pixel whose pooled vector is read,
+    // t - t_ref, 1 for a valid event (0 otherwise) and the output row code.
+    // Rows past the end and invalid events read pixel 0: the MMA keeps rows
+    // apart and their results are discarded.
+    auto meta = [&](int li, int &pix, uint32_t &trel, float &inv, int &outk) {
+      const int i = ((int)blockIdx.x + li * (int)gridDim.x) * kM + row;
+      pix = 0;
+      trel = 0;
+      inv = 0.f;
+      outk = -1;
+      if (i >= ns) return;
+      if (rec) {
+        const int2 r = __ldg(rec + i);
+        pix = __ldg(rpix + i);
+        trel = (uint32_t)r.x;
+        outk = r.y;
+        inv = 1.f;
+        return;
+      }
+      int64_t k = i;
+      if (K) {
+        k = K[i];
+        if (k < 0 || k >= ev.n) {
+          atomicOr(err, ERR_INDEX_RANGE);
+          outk = invalid_row(i);
+          return;
+        }
+      }
+      const int x = ev.x[k], y = ev.y[k];
+      const uint32_t tt = ev.t[k];
+      trel = tt - ev.t_ref;
+      if (x >= 0 && x < g.W && y >= 0 && y < g.H && tt >= ev.t_ref && trel <= ev.t_span) {
+        pix = y * g.W + x;
+        outk = i;
+        inv = 1.f;
+      } else {
+        outk = invalid_row(i);
+      }
+    };
+    // The row's units stream through a ring of R registers: unit u is loaded
+    // R - 1 units ahead of its use, the last ones from the next tile's row
+    // (32 is a multiple of R, so a tile's unit v sits in ring slot v mod R
+    // whichever tile it belongs to).
+    constexpr int R = HALF ? 16 : 8;
+    static_assert(U % R == 0, "the ring wraps at a row's end");
+    Q ring[R];
+    int c_pix = 0, c_outk = -1;
+    uint32_t c_trel = 0;
+    float c_inv = 0.f;
+    if (pg < nlocal) {
+      meta(pg, c_pix, c_trel, c_inv, c_outk);
+      const Q *prow = pooled + (size_t)c_pix * U;
+#pragma unroll
+      for (int v = 0; v < R - 1; ++v) ring[v] = __ldg(prow + v);
+    }
+    int c_cnt = (!HALF && pg < nlocal && c_inv != 0.f) ? __ldg(ncnt + c_pix) : 0;
+    for (int li = pg; li < nlocal && ok; li += kTmProdGroups) {
+      const bool has_next = li + kTmProdGroups < nlocal;
+      int n_pix = 0, n_outk = -1;
+      uint32_t n_trel = 0;
+      float n_inv = 0.f;
+      if (has_next) meta(li + kTmProdGroups, n_pix, n_trel, n_inv, n_outk);
+      // the A slot is free once this group's previous tile's first layer has run
+      if (li >= kTmProdGroups && !mbar_wait(done_bar(pg), ((li / 4) - 1) & 1, wl)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const Q *prow = pooled + (size_t)c_pix * U;
+      const Q *nrow = pooled + (size_t)n_pix * U;
+      int n_cnt = 0;
+      uint32_t pk[8];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        // the load R - 1 units ahead
+        const int ua = u + R - 1;
+        if (ua < U) ring[ua % R] = __ldg(prow + ua);
+        else if (has_next) ring[ua % R] = __ldg(nrow + (ua - U));
+        if (!HALF && u == U / 2 && has_next && n_inv != 0.f) n_cnt = __ldg(ncnt + n_pix);
+        const Q q = ring[u % R];
+        const uint4 w = sWt[u];
+        const float4 ph = time_phase2_packed(c_trel, make_uint2(w.x, w.y), make_uint2(w.z, w.w));
+        uint32_t wre, wim;
+        if constexpr (HALF) {
+          const __half2 PR = *reinterpret_cast<const __half2 *>(&q.x);
+          const __half2 PI = *reinterpret_cast<const __half2 *>(&q.y);
+          const __half2 C = __floats2half2_rn(ph.x, ph.z);
+          const __half2 S = __floats2half2_rn(ph.y, ph.w);
+          const __half2 ER = __hfma2(PR, C, __hmul2(PI, S));
+          const __half2 EI = __hfma2(PI, C, __hneg2(__hmul2(PR, S)));
+          if (fp16) {
+            wre = *reinterpret_cast<const uint32_t *>(&ER);
+            wim = *reinterpret_cast<const uint32_t *>(&EI);
+          } else {
+            const float2 fr = __half22float2(ER), fi = __half22float2(EI);
+            wre = pack2(fr.x, fr.y, 0);
+            wim = pack2(fi.x, fi.y, 0);
+          }
+        } else {
+          const float2 Rr = make_float2(q.x, q.y);
+          const float2 I = make_float2(q.z, q.w);
+          const float2 C = make_float2(ph.x, ph.z), S = make_float2(ph.y, ph.w);
+          const float2 er = ffma2(Rr, C, fmul2(I, S));
+          const float2 ei = fsub2(fmul2(I, C), fmul2(Rr, S));
+          wre = pack2(er.x, er.y, fp16);
+          wim = pack2(ei.x, ei.y, fp16);
+        }
+        pk[2 * (u & 3)] = wre;
+        pk[2 * (u & 3) + 1] = wim;
+        if ((u & 3) == 3) {
+          // unit u - 3 + j in columns 2(u - 3 + j) (Re pair) and 2(u - 3 + j) + 1
+          // (Im pair): K = 4u' .. 4u'+3 for unit u'
+          asm volatile(
+              "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+                  a_t + (uint32_t)(2 * (u - 3))),
+              "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3]), "r"(pk[4]), "r"(pk[5]), "r"(pk[6]),
+              "r"(pk[7])
+              : "memory");
+        }
+      }
+      const int msl = li % kTmMeta;
+      sK[msl * kM + row] = c_outk;
+      sInv[msl * kM + row] = (!HALF && c_inv != 0.f) ? 1.0f / (float)c_cnt : c_inv;
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      // (the stall injection of the error-path tests withholds this signal)
+      if (lane == 0 && !mlp.inject_stall) mbar_arrive(full_bar(pg));
+      c_pix = n_pix;
+      c_trel = n_trel;
+      c_inv = n_inv;
+      c_outk = n_outk;
+      c_cnt = n_cnt;
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int grp = warp >> 2;        // tiles li = grp mod 2, accumulator grp
+    const bool issuer = (warp & 3) == 0;
+    const float b20 = ep.b2[0], b21 = ep.b2[1];
+    constexpr uint32_t idesc_bf16 = make_idesc(0, kM, kN);
+    constexpr uint32_t idesc_fp16 = make_idesc(1, kM, kN);
+    const uint32_t idesc = fp16 ? idesc_fp16 : idesc_bf16;
+    constexpr uint32_t idesc2 = make_idesc(1, kM, kN2);
+    const uint32_t sB_a = smem_u32(sB), sW2_a = smem_u32(sW2);
+    const uint32_t acc_col = (uint32_t)(kTmAccBase + grp * kN);
+    // this CTA's share [z0, z1) of the buffer to zero, one slice per tile
+    int64_t z0 = 0, z1 = 0, zstep = 0;
+    if (zero_buf) {
+      const int64_t per_cta = (zero_units + gridDim.x - 1) / gridDim.x;
+      z0 = (int64_t)blockIdx.x * per_cta < zero_units ? (int64_t)blockIdx.x * per_cta : zero_units;
+      z1 = z0 + per_cta < zero_units ? z0 + per_cta : zero_units;
+      zstep = nlocal > 0 ? (z1 - z0 + nlocal - 1) / nlocal : 0;
+    }
+    auto zero_slice = [&](int c) {
+      const int64_t a = z0 + (int64_t)c * zstep, e = a + zstep < z1 ? a + zstep : z1;
+      for (int64_t u = a + row; u < e; u += 4 * 32) zero_buf[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    int li = grp;
+    for (; li < nlocal && ok; li += kTmEpiGroups) {
+      const int sa = li & 3;             // A slot and its barriers
+      const uint32_t pa = (li >> 2) & 1;  // their phase parity for this tile
+      const uint32_t pg2 = (li >> 1) & 1; // this group's barriers' parity
+      if (issuer) {
+        // the tile filled, and this group's accumulator read back (tile li - 2)
+        if (!mbar_wait(full_bar(sa), pa, wl) ||
+            (li >= kTmEpiGroups && !mbar_wait(empty_bar(grp), pg2 ^ 1, wl))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (lane == 0) {
+          const uint32_t a_tm = tmem + (uint32_t)(sa * kTmACols);
+#pragma unroll
+          for (int kk = 0; kk < IN / 16; ++kk) {
+            const uint32_t koff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
+            const uint64_t bd = make_desc_sw128(sB_a + koff);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem +
+                                                                                    acc_col),
+                "r"(a_tm + (uint32_t)(kk * 8)), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  done_bar(sa))
+              : "memory");
+        }
+        __syncwarp();
+      }
+      // done: the first layer's accumulator (and the A slot is free)
+      if (!mbar_wait(done_bar(sa), pa, wl)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int msl = li % kTmMeta;
+      const float inv = sInv[msl * kM + row];
+      const int k = sK[msl * kM + row];
+      const float2 inv2 = make_float2(inv, inv);
+      const uint32_t acc_t = tmem + lane_base + acc_col;
+#pragma unroll
+      for (int c0 = 0; c0 < kN; c0 += 32) {
+        float h[32];
+        tmem_ld32(acc_t + c0, h);
+        uint32_t pk[16];
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 bb = *reinterpret_cast<const float4 *>(ep.b1 + c0 + j);
+          const float2 a01 = ffma2(make_float2(h[j], h[j + 1]), inv2, make_float2(bb.x, bb.y));
+          const float2 a23 = ffma2(make_float2(h[j + 2], h[j + 3]), inv2, make_float2(bb.z, bb.w));
+          pk[j / 2] = relu_f16x2(a01.x, a01.y);
+          pk[j / 2 + 1] = relu_f16x2(a23.x, a23.y);
+        }
+        tmem_st16(acc_t + c0 / 2, pk);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(stored_bar(grp));
+      if (issuer) {
+        if (!mbar_wait(stored_bar(grp), pg2, wl)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (lane == 0) {
+          const uint32_t a2 = tmem + acc_col;
+#pragma unroll
+          for (int kk = 0; kk < kN / 16; ++kk) {
+            const uint64_t bd = make_desc_sw128(sW2_a + (kk >> 2) * (kN2 * 128) + (kk & 3) * 32);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(a2 +
+                                                                                    kOutCol),
+                "r"(a2 + (uint32_t)(kk * 8)), "l"(bd), "r"(idesc2), "r"(acc)
+                : "memory");
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  out_bar(grp))
+              : "memory");
+        }
+        __syncwarp();
+      }
+      if (!mbar_wait(out_bar(grp), pg2, wl)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t r0, r1;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                   : "=r"(r0), "=r"(r1)
+                   : "r"(acc_t + kOutCol));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty_bar(grp));
+      if (k >= 0) {
+        *reinterpret_cast<float2 *>(flow + 2 * (size_t)k) =
+            make_float2(__uint_as_float(r0) + b20, __uint_as_float(r1) + b21);
+      } else if (k <= -2) {
+        *reinterpret_cast<float2 *>(flow + 2 * (size_t)(-2 - k)) = make_float2(0.f, 0.f);
+      }
+      if (zero_buf) zero_slice(li);
+    }
+    if (zero_buf)
+      for (; li < nlocal; li += kTmEpiGroups) zero_slice(li);
+    if (issuer) {
+      // every MMA this warp issued has landed before the tensor memory is freed
+      if (lane == 0)
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                drain_bar(grp))
+            : "memory");
+      __syncwarp();
+      if (!mbar_wait(drain_bar(grp), 0, wl)) ok = false;
+    }
+  }
+  if (!ok && lane == 0) atomicOr(err, ERR_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmCols));
+  }
+}
+
+template <bool HALF, bool F16>
+int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
+                    const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
+                    const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
+                    cudaStream_t s, float4 *zero_buf, int64_t zero_units, bool *zeroed) {
+  if (zeroed) *zeroed = false;
+  if (nK == 0) return 0;
+  constexpr int IN = 128;
+  const size_t sm = (size_t)kN * IN * 2 + kW2Bytes + (sizeof(float) + sizeof(int)) * kTmMeta * kM +
+                    16 * 32 + 8 * 16 + 16 + 1024;  // + SW128 alignment slack
+  auto kern = k_predict_tm<HALF, F16>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+      cudaSuccess)
+    return -1;
+  const int64_t tiles = (nK + kM - 1) / kM;
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms());
+  constexpr int64_t kZeroPerTile = 8192;
+  const int64_t min_local = tiles / grid;
+  const bool zero = zero_buf && zero_units > 0 &&
+                    (zero_units + grid - 1) / grid <= min_local * kZeroPerTile;
+  EpiParams ep;
+  std::copy(mlp.hb1, mlp.hb1 + kN, ep.b1);
+  ep.b2[0] = mlp.hb2[0];
+  ep.b2[1] = mlp.hb2[1];
+  kern<<<grid, kTmThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
+                                    err, zero ? zero_buf : nullptr, zero ? zero_units : 0, ep);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (zeroed) *zeroed = zero;
+  return 1;
+}
+
 }  // namespace
 
 int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
@@ -770,21 +1193,25 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
                       int *err, cudaStream_t s, const Tune &tn, float4 *zero_buf,
                       int64_t zero_units, bool *zeroed) {
   const bool h = mlp.pooled_half != 0, f16 = mlp.half_kind != 0;
-#define VECKM_TC(DV_, H_, F_)                                                                    \
-  predict_tc_impl<DV_, H_, F_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, \
-                               s, tn.tc_ctas, zero_buf, zero_units, zeroed)
-#define VECKM_TC2(DV_, H_) (f16 ? VECKM_TC(DV_, H_, true) : VECKM_TC(DV_, H_, false))
+#define VECKM_TM(H_, F_)                                                                    \
+  predict_tm_impl<H_, F_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, s, \
+                          zero_buf, zero_units, zeroed)
+#define VECKM_TC(H_, F_)                                                                    \
+  predict_tc_impl<2, H_, F_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err, \
+                             s, zero_buf, zero_units, zeroed)
   if (zeroed) *zeroed = false;
   switch (g.U / 32) {
     case 1:
-      return h ? VECKM_TC2(1, true) : VECKM_TC2(1, false);
+      if (h) return f16 ? VECKM_TM(true, true) : VECKM_TM(true, false);
+      return f16 ? VECKM_TM(false, true) : VECKM_TM(false, false);
     case 2:
-      return h ? VECKM_TC2(2, true) : VECKM_TC2(2, false);
+      if (h) return f16 ? VECKM_TC(true, true) : VECKM_TC(true, false);
+      return f16 ? VECKM_TC(false, true) : VECKM_TC(false, false);
     default:
       return -1;  // 2D > 256 does not fit the operand tiles in shared memory
   }
-#undef VECKM_TC2
 #undef VECKM_TC
+#undef VECKM_TM
 }
 
 }  // namespace veckm

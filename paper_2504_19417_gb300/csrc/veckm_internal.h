@@ -64,7 +64,6 @@ struct MLP {
 struct Tune {
   int rows_seg = 0, rows_wpb = 0;  // row pass: segment length in windows, warps per block
   int cols_seg = 0, cols_wpb = 0;  // column pass: the same
-  int tc_ctas = 0;                 // tensor-core head: CTAs per SM (1 or 2)
 };
 
 // Launchers (kernels.cu, mlp_tc.cu).  Each returns the number of kernels it
