@@ -669,8 +669,7 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
       int prev = __shfl_up_sync(kFull, pl, 1);
       if (lane == 0) prev = sp;
       const unsigned starts = __ballot_sync(kFull, lane < m && pl != prev);
-#pragma unroll 4
-      for (int j = 0; j < m; ++j) {
+      auto step = [&](int j) {
         const uint32_t tj = __shfl_sync(kFull, tl, j);
         if ((starts >> j) & 1u) {
           if (sp >= 0) {
@@ -683,6 +682,14 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
         }
 #pragma unroll
         for (int v = 0; v < DV; ++v) s[v] = add4x2(s[v], time_phase2_packed(tj, w[v][0], w[v][1]));
+      };
+      if (m == 32) {
+        // a full group: the record positions are known at compile time
+#pragma unroll
+        for (int j = 0; j < 32; ++j) step(j);
+      } else {
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) step(j);
       }
     }
     // the last range's last pixel, when it started inside the range, has no

@@ -1,7 +1,8 @@
 """GPU tests of the sort by pixel that feeds the per-pixel sums (the bucket
 form): a bucket holding more records than its shared-memory stage (placed
-straight into its region instead), and a slice of more than 4096 x 4096
-events (tiles of 8192 events).  Encodings are checked against the FP64
+straight into its region instead), a slice of more than 4096 x 4096
+events (tiles of 8192 events), and a slice beyond the bucket form's limits
+(histogram, scan and placement).  Encodings are checked against the FP64
 oracle's pooled form (Algorithm 1, Eq. 16-17) on the same events."""
 import numpy as np
 import pytest
@@ -52,5 +53,21 @@ def test_more_events_than_one_round_of_tiles():
     x, y, t = to_dev(sl)
     K = np.sort(np.random.default_rng(6).choice(n, 2_000, replace=False)).astype(np.int64)
     emb = enc.encode(x, y, t, sl.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
+    assert emb_rel_err(emb, _ref(sl, TXY, K)).max() <= EMB_TOL_FP32
+    enc.sync_status()
+
+
+def test_histogram_sort_above_the_bucket_limits():
+    # 34 M events (more than 2 x 4096 tiles of 8192): the histogram, scan and
+    # placement form of the sort, whose exclusive prefix gives the row
+    # offsets of the per-pixel sums; dense path forced for the sampled requests
+    n = 34_000_000
+    sl = synth.event_slice(160, 120, n, 20_000, n_edges=6, seed=503)
+    enc, TXY, _ = make(sl, D, t_span_us=20_000)
+    enc.set_path(vk.PATH_DENSE)
+    x, y, t = to_dev(sl)
+    K = np.sort(np.random.default_rng(7).choice(n, 1_000, replace=False)).astype(np.int64)
+    emb = enc.encode(x, y, t, sl.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
+    assert enc.last_path() == vk.PATH_DENSE
     assert emb_rel_err(emb, _ref(sl, TXY, K)).max() <= EMB_TOL_FP32
     enc.sync_status()
