@@ -775,16 +775,45 @@ int predict_tc_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
 // k_predict_tc.  No operand tile takes shared memory, so four tiles can be in
 // production at once and a producer group waits only for its own previous
 // tile's first layer.
-constexpr int kTmProdGroups = 4;
 constexpr int kTmEpiGroups = 2;
-constexpr int kTmThreads = 32 * 4 * (kTmProdGroups + kTmEpiGroups);
-constexpr int kTmACols = 64;   // A slot: 128 K values as FP16 pairs
-constexpr int kTmAccBase = kTmProdGroups * kTmACols;  // accumulators after the A slots
+constexpr int kTmACols = 64;     // A slot: 128 K values as FP16 pairs
+constexpr int kTmAccBase = 256;  // accumulators after (at most four) A slots
 constexpr int kTmCols = 512;
-constexpr int kTmMeta = 8;     // row-metadata slots (tile li in li mod 8)
+// P producer groups of 4 warps
+template <int P>
+struct TmShape {
+  static_assert(P >= 2 && P <= 4, "A slots: P x 64 columns before the accumulators");
+  static constexpr int warps = 4;  // per producer group
+  static constexpr int threads = 32 * (warps * P + 4 * kTmEpiGroups);
+  // Row-metadata slots: tile li in slot li mod (P + 2).  The slot of tile li
+  // is rewritten at the end of tile li + P + 2's production, which starts
+  // once tile li + 2's first layer has run; that was issued once every warp
+  // of li's epilogue group (tile li + 2 is in the same group) had read tile
+  // li back, metadata included.
+  static constexpr int meta = P + 2;
+  // Tile li signals full[li mod ring] (producers -> issuer) and
+  // done[li mod ring] (first layer -> its epilogue group and the producer
+  // group that fills the same A slot next, tile li + P).  ring = lcm(P, 2):
+  // the tiles of one barrier, li and li + ring, then share both the producer
+  // group and the epilogue group, so every waiter waits for each phase in
+  // turn, and the phase of li + ring cannot complete before every waiter of
+  // li's phase has passed it (li + ring's first layer waits for li's group
+  // to have read tile li + ring - 2 back, and its producers for li + ring - P's
+  // first layer).  With one barrier per A slot and P odd, consecutive phases
+  // would alternate between the epilogue groups, and a group waiting for
+  // every other phase could take the parity of a phase not yet completed
+  // for its own.
+  static constexpr int ring = P % 2 == 0 ? P : 2 * P;
+  static constexpr int bars = 2 * ring + 8;
+};
 
-template <bool HALF, bool F16>
-__global__ void __launch_bounds__(kTmThreads, 1)
+// The shape launched: four producer groups.  (On the 640 x 480, 2 M event
+// slice, three groups of 8 warps that fill half a row each per thread ran
+// 151 us and two such groups 189 us, against 149 us for this one.)
+constexpr int kTmP = 4;
+
+template <bool HALF, bool F16, int P>
+__global__ void __launch_bounds__(TmShape<P>::threads, 1)
     k_predict_tm(Events ev, const int64_t *__restrict__ K, int64_t nK,
                  const int2 *__restrict__ rec, const int *__restrict__ rpix,
                  const int *__restrict__ nsorted, Geometry g, Tables tb,
@@ -798,12 +827,14 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sB = smem;                       // [128 x IN] half (W1), SW128
   uint8_t *sW2 = sB + W1_BYTES;             // [16 x 128] FP16 (W2 padded), SW128
-  float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);  // [kTmMeta][128] 1/n (or 1), 0 invalid
-  int *sK = reinterpret_cast<int *>(sInv + kTmMeta * kM);    // [kTmMeta][128] output row codes
-  uint4 *sWt = reinterpret_cast<uint4 *>(sK + kTmMeta * kM); // [32] frequencies of channels 2u, 2u+1
-  // full[4], done[4], stored[2], out[2], empty[2], drain[2]
+  constexpr int kMeta = TmShape<P>::meta;
+  float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);  // [kMeta][128] 1/n (or 1), 0 invalid
+  int *sK = reinterpret_cast<int *>(sInv + kMeta * kM);      // [kMeta][128] output row codes
+  uint4 *sWt = reinterpret_cast<uint4 *>(sK + kMeta * kM);   // [32] frequencies of channels 2u, 2u+1
+  // full[ring], done[ring], stored[2], out[2], empty[2], drain[2]
+  constexpr int kRing = TmShape<P>::ring, kB = 2 * kRing;
   uint64_t *bars = reinterpret_cast<uint64_t *>(sWt + U);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 16);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + TmShape<P>::bars);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int fp16 = F16 ? 1 : 0;
@@ -818,16 +849,18 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     if (tid < U) sWt[tid] = __ldg(reinterpret_cast<const uint4 *>(tb.wt) + tid);
   }
   const uint32_t bar0 = smem_u32(bars);
-  auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto done_bar = [&](int s) { return bar0 + 8u * (4 + s); };
-  auto stored_bar = [&](int g) { return bar0 + 8u * (8 + g); };
-  auto out_bar = [&](int g) { return bar0 + 8u * (10 + g); };
-  auto empty_bar = [&](int g) { return bar0 + 8u * (12 + g); };
-  auto drain_bar = [&](int g) { return bar0 + 8u * (14 + g); };
+  auto full_bar = [&](int li) { return bar0 + 8u * (li % kRing); };           // of tile li
+  auto done_bar = [&](int li) { return bar0 + 8u * (kRing + li % kRing); };  // of tile li
+  auto stored_bar = [&](int g) { return bar0 + 8u * (kB + g); };
+  auto out_bar = [&](int g) { return bar0 + 8u * (kB + 2 + g); };
+  auto empty_bar = [&](int g) { return bar0 + 8u * (kB + 4 + g); };
+  auto drain_bar = [&](int g) { return bar0 + 8u * (kB + 6 + g); };
+  auto ring_par = [&](int li) { return (uint32_t)(li / kRing) & 1u; };  // tile li's phase parity
   if (tid == 0) {
-    for (int s = 0; s < 4; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(full_bar(s)));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_bar(s)));
+    for (int d = 0; d < kRing; ++d) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full_bar(d)),
+                   "r"(TmShape<P>::warps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_bar(d)));
     }
     for (int g2 = 0; g2 < 2; ++g2) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(stored_bar(g2)));
@@ -859,7 +892,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
 
   if (warp >= 4 * kTmEpiGroups) {
     // ------------------------------------------------------------ producers
-    const int pg = (warp - 4 * kTmEpiGroups) >> 2;  // tiles li = pg mod 4, A slot pg
+    const int pg = (warp - 4 * kTmEpiGroups) / TmShape<P>::warps;  // tiles li = pg mod P, A slot pg
     using Q = typename std::conditional<HALF, uint2, float4>::type;
     const Q *pooled = reinterpret_cast<const Q *>(pooled_v);
     const uint32_t a_t = tmem + lane_base + (uint32_t)(pg * kTmACols);
@@ -919,14 +952,14 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       for (int v = 0; v < R - 1; ++v) ring[v] = __ldg(prow + v);
     }
     int c_cnt = (!HALF && pg < nlocal && c_inv != 0.f) ? __ldg(ncnt + c_pix) : 0;
-    for (int li = pg; li < nlocal && ok; li += kTmProdGroups) {
-      const bool has_next = li + kTmProdGroups < nlocal;
+    for (int li = pg; li < nlocal && ok; li += P) {
+      const bool has_next = li + P < nlocal;
       int n_pix = 0, n_outk = -1;
       uint32_t n_trel = 0;
       float n_inv = 0.f;
-      if (has_next) meta(li + kTmProdGroups, n_pix, n_trel, n_inv, n_outk);
+      if (has_next) meta(li + P, n_pix, n_trel, n_inv, n_outk);
       // the A slot is free once this group's previous tile's first layer has run
-      if (li >= kTmProdGroups && !mbar_wait(done_bar(pg), ((li / 4) - 1) & 1, wl)) {
+      if (li >= P && !mbar_wait(done_bar(li - P), ring_par(li - P), wl)) {
         ok = false;
         break;
       }
@@ -950,9 +983,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
           const __half2 PR = *reinterpret_cast<const __half2 *>(&q.x);
           const __half2 PI = *reinterpret_cast<const __half2 *>(&q.y);
           const __half2 C = __floats2half2_rn(ph.x, ph.z);
-          const __half2 S = __floats2half2_rn(ph.y, ph.w);
-          const __half2 ER = __hfma2(PR, C, __hmul2(PI, S));
-          const __half2 EI = __hfma2(PI, C, __hneg2(__hmul2(PR, S)));
+          const __half2 Sn = __floats2half2_rn(ph.y, ph.w);
+          const __half2 ER = __hfma2(PR, C, __hmul2(PI, Sn));
+          const __half2 EI = __hfma2(PI, C, __hneg2(__hmul2(PR, Sn)));
           if (fp16) {
             wre = *reinterpret_cast<const uint32_t *>(&ER);
             wim = *reinterpret_cast<const uint32_t *>(&EI);
@@ -964,9 +997,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
         } else {
           const float2 Rr = make_float2(q.x, q.y);
           const float2 I = make_float2(q.z, q.w);
-          const float2 C = make_float2(ph.x, ph.z), S = make_float2(ph.y, ph.w);
-          const float2 er = ffma2(Rr, C, fmul2(I, S));
-          const float2 ei = fsub2(fmul2(I, C), fmul2(Rr, S));
+          const float2 C = make_float2(ph.x, ph.z), Sn = make_float2(ph.y, ph.w);
+          const float2 er = ffma2(Rr, C, fmul2(I, Sn));
+          const float2 ei = fsub2(fmul2(I, C), fmul2(Rr, Sn));
           wre = pack2(er.x, er.y, fp16);
           wim = pack2(ei.x, ei.y, fp16);
         }
@@ -983,14 +1016,14 @@ __global__ void __launch_bounds__(kTmThreads, 1)
               : "memory");
         }
       }
-      const int msl = li % kTmMeta;
+      const int msl = li % kMeta;
       sK[msl * kM + row] = c_outk;
       sInv[msl * kM + row] = (!HALF && c_inv != 0.f) ? 1.0f / (float)c_cnt : c_inv;
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       // (the stall injection of the error-path tests withholds this signal)
-      if (lane == 0 && !mlp.inject_stall) mbar_arrive(full_bar(pg));
+      if (lane == 0 && !mlp.inject_stall) mbar_arrive(full_bar(li));
       c_pix = n_pix;
       c_trel = n_trel;
       c_inv = n_inv;
@@ -1022,12 +1055,11 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     };
     int li = grp;
     for (; li < nlocal && ok; li += kTmEpiGroups) {
-      const int sa = li & 3;             // A slot and its barriers
-      const uint32_t pa = (li >> 2) & 1;  // their phase parity for this tile
+      const int sa = li % P;  // A slot
       const uint32_t pg2 = (li >> 1) & 1; // this group's barriers' parity
       if (issuer) {
         // the tile filled, and this group's accumulator read back (tile li - 2)
-        if (!mbar_wait(full_bar(sa), pa, wl) ||
+        if (!mbar_wait(full_bar(li), ring_par(li), wl) ||
             (li >= kTmEpiGroups && !mbar_wait(empty_bar(grp), pg2 ^ 1, wl))) {
           ok = false;
           break;
@@ -1049,27 +1081,29 @@ __global__ void __launch_bounds__(kTmThreads, 1)
           }
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  done_bar(sa))
+                  done_bar(li))
               : "memory");
         }
         __syncwarp();
       }
       // done: the first layer's accumulator (and the A slot is free)
-      if (!mbar_wait(done_bar(sa), pa, wl)) {
+      if (!mbar_wait(done_bar(li), ring_par(li), wl)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int msl = li % kTmMeta;
+      const int msl = li % kMeta;
       const float inv = sInv[msl * kM + row];
       const int k = sK[msl * kM + row];
       const float2 inv2 = make_float2(inv, inv);
       const uint32_t acc_t = tmem + lane_base + acc_col;
+      // ReLU(h / n + b1) as FP16 pairs into columns [0, kN/2): chunk c0
+      // reads [c0, c0 + 32) and writes [c0/2, c0/2 + 16), already read
 #pragma unroll
       for (int c0 = 0; c0 < kN; c0 += 32) {
         float h[32];
-        tmem_ld32(acc_t + c0, h);
         uint32_t pk[16];
+        tmem_ld32(acc_t + c0, h);
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           const float4 bb = *reinterpret_cast<const float4 *>(ep.b1 + c0 + j);
@@ -1123,11 +1157,15 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(empty_bar(grp));
-      if (k >= 0) {
+      // (row codes come from this launch's metadata: k < nK, -2 - k < nK;
+      // a code outside them is recorded and not written)
+      if (k >= 0 && k < nK) {
         *reinterpret_cast<float2 *>(flow + 2 * (size_t)k) =
             make_float2(__uint_as_float(r0) + b20, __uint_as_float(r1) + b21);
-      } else if (k <= -2) {
+      } else if (k <= -2 && -2 - (int64_t)k < nK) {
         *reinterpret_cast<float2 *>(flow + 2 * (size_t)(-2 - k)) = make_float2(0.f, 0.f);
+      } else if (k != -1) {
+        atomicOr(err, ERR_INDEX_RANGE);
       }
       if (zero_buf) zero_slice(li);
     }
@@ -1162,9 +1200,11 @@ int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128;
-  const size_t sm = (size_t)kN * IN * 2 + kW2Bytes + (sizeof(float) + sizeof(int)) * kTmMeta * kM +
-                    16 * 32 + 8 * 16 + 16 + 1024;  // + SW128 alignment slack
-  auto kern = k_predict_tm<HALF, F16>;
+  constexpr int P = kTmP;
+  const size_t sm = (size_t)kN * IN * 2 + kW2Bytes +
+                    (sizeof(float) + sizeof(int)) * TmShape<P>::meta * kM +
+                    16 * 32 + 8 * TmShape<P>::bars + 16 + 1024;  // + SW128 alignment slack
+  auto kern = k_predict_tm<HALF, F16, P>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
     return -1;
@@ -1178,7 +1218,7 @@ int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   std::copy(mlp.hb1, mlp.hb1 + kN, ep.b1);
   ep.b2[0] = mlp.hb2[0];
   ep.b2[1] = mlp.hb2[1];
-  kern<<<grid, kTmThreads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
+  kern<<<grid, TmShape<P>::threads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
                                     err, zero ? zero_buf : nullptr, zero ? zero_units : 0, ep);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   if (zeroed) *zeroed = zero;
