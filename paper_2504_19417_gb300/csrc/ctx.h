@@ -58,6 +58,7 @@ struct veckm_ctx {
   int64_t rec_cap = 0;
   std::vector<float> hW1;  // host copy (re-encoding on precision switch)
   std::vector<float> hb1, hW2, hb2;  // host copies (kernel parameters)
+  std::vector<uint2> hwt;            // host copy of wt (a kernel parameter of the D = 64 head)
   // staging for the host-buffer entry point
   void *st_buf = nullptr;
   size_t st_cap = 0;
@@ -106,7 +107,7 @@ struct veckm_ctx {
   veckm::MLP mlp() const {
     return veckm::MLP{W1,     W1t, b1, W2, b2, W1h, hidden, (flags & VECKM_MLP_FP16) ? 1 : 0, 0,
                       hb1.data(), hW2.data(), hb2.data(), W2h, wait_cycles,
-                      inject == VECKM_INJECT_HEAD_STALL ? 1 : 0};
+                      inject == VECKM_INJECT_HEAD_STALL ? 1 : 0, hwt.data()};
   }
 };
 

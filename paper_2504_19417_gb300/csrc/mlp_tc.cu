@@ -82,10 +82,13 @@ constexpr int kN2 = 16;
 constexpr int kOutCol = kN / 2;
 constexpr int kW2Bytes = kN2 * kN * 2;  // W2 as FP16, K-major, 128-byte swizzled
 
-// First-layer bias and second-layer bias, by value.
+// First-layer bias and second-layer bias, by value; for the D = 64 head also
+// the fixed-point temporal frequencies of channels 2u, 2u+1 (wt[2u], wt[2u+1]
+// as one uint4 per unit), read as constant operands of the phase arithmetic.
 struct __align__(16) EpiParams {
   float b1[kN];
   float b2[2];
+  uint4 wt[32];
 };
 // Output row codes (event counts are below 2^30): k >= 0 writes the flow of
 // row k; -1 writes nothing; k <= -2 writes zeros to row -2 - k (an invalid
@@ -830,23 +833,21 @@ __global__ void __launch_bounds__(TmShape<P>::threads, 1)
   constexpr int kMeta = TmShape<P>::meta;
   float *sInv = reinterpret_cast<float *>(sW2 + kW2Bytes);  // [kMeta][128] 1/n (or 1), 0 invalid
   int *sK = reinterpret_cast<int *>(sInv + kMeta * kM);      // [kMeta][128] output row codes
-  uint4 *sWt = reinterpret_cast<uint4 *>(sK + kMeta * kM);   // [32] frequencies of channels 2u, 2u+1
   // full[ring], done[ring], stored[2], out[2], empty[2], drain[2]
   constexpr int kRing = TmShape<P>::ring, kB = 2 * kRing;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sWt + U);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sK + kMeta * kM);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + TmShape<P>::bars);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int fp16 = F16 ? 1 : 0;
   const long long wl = mlp.wait_cycles;
-  {  // W1, W2 (already in SW128 order) and the temporal frequencies
+  {  // W1 and W2 (already in SW128 order)
     const uint4 *src = reinterpret_cast<const uint4 *>(mlp.W1h);
     uint4 *dst = reinterpret_cast<uint4 *>(sB);
     for (int i = tid; i < W1_BYTES / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     const uint4 *src2 = reinterpret_cast<const uint4 *>(mlp.W2h);
     uint4 *dst2 = reinterpret_cast<uint4 *>(sW2);
     for (int i = tid; i < kW2Bytes / 16; i += blockDim.x) dst2[i] = __ldg(src2 + i);
-    if (tid < U) sWt[tid] = __ldg(reinterpret_cast<const uint4 *>(tb.wt) + tid);
   }
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int li) { return bar0 + 8u * (li % kRing); };           // of tile li
@@ -975,8 +976,15 @@ __global__ void __launch_bounds__(TmShape<P>::threads, 1)
         if (ua < U) ring[ua % R] = __ldg(prow + ua);
         else if (has_next) ring[ua % R] = __ldg(nrow + (ua - U));
         if (!HALF && u == U / 2 && has_next && n_inv != 0.f) n_cnt = __ldg(ncnt + n_pix);
+        // the next row's pooled values into L2 a tile ahead of their loads
+        // (its pixel has arrived by now)
+        if (u == 8 && has_next) {
+#pragma unroll
+          for (int l = 0; l < (int)(U * sizeof(Q)) / 128; ++l)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(nrow) + 128 * l));
+        }
         const Q q = ring[u % R];
-        const uint4 w = sWt[u];
+        const uint4 w = ep.wt[u];
         const float4 ph = time_phase2_packed(c_trel, make_uint2(w.x, w.y), make_uint2(w.z, w.w));
         uint32_t wre, wim;
         if constexpr (HALF) {
@@ -1203,7 +1211,7 @@ int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   constexpr int P = kTmP;
   const size_t sm = (size_t)kN * IN * 2 + kW2Bytes +
                     (sizeof(float) + sizeof(int)) * TmShape<P>::meta * kM +
-                    16 * 32 + 8 * TmShape<P>::bars + 16 + 1024;  // + SW128 alignment slack
+                    8 * TmShape<P>::bars + 16 + 1024;  // + SW128 alignment slack
   auto kern = k_predict_tm<HALF, F16, P>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
@@ -1218,6 +1226,10 @@ int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   std::copy(mlp.hb1, mlp.hb1 + kN, ep.b1);
   ep.b2[0] = mlp.hb2[0];
   ep.b2[1] = mlp.hb2[1];
+  if (!mlp.hwt) return -1;
+  for (int u = 0; u < 32; ++u)
+    ep.wt[u] = make_uint4(mlp.hwt[2 * u].x, mlp.hwt[2 * u].y, mlp.hwt[2 * u + 1].x,
+                          mlp.hwt[2 * u + 1].y);
   kern<<<grid, TmShape<P>::threads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,
                                     err, zero ? zero_buf : nullptr, zero ? zero_units : 0, ep);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;

@@ -549,6 +549,7 @@ veckm_status veckm_create(veckm_ctx **out, const veckm_config *cfg) {
     hwxy[d] = fixed_turns(c->X[d] * wx);
     hwxy[D + d] = fixed_turns(c->Y[d] * wy);
   }
+  c->hwt = hwt;
   const int IN = 2 * D;
   c->hW1.assign(cfg->h_W1, cfg->h_W1 + (size_t)c->hidden * IN);
   c->hb1.assign(cfg->h_b1, cfg->h_b1 + c->hidden);

@@ -57,6 +57,9 @@ struct MLP {
   // injection that stops its producers from signalling filled tiles
   long long wait_cycles = 4000000000LL;
   int inject_stall = 0;
+  // host copy of the fixed-point temporal frequencies (Tables::wt), passed
+  // to the D = 64 tensor-core head as a kernel parameter
+  const uint2 *hwt = nullptr;
 };
 
 // Launch shapes picked by the autotuner (batch.cu); 0 keeps the built-in
