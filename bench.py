@@ -448,11 +448,19 @@ def run_ours(args):
     out["kernels"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                           for kk, vv in v.items()} for k, v in kern.items()}
     encoder_ms = sum(kern[k]["ms"] for k in kern if k != "gather")
+    # the survey's per-stage model: events read once (9 B each), the
+    # per-pixel accumulator (8D + 4 B) written once and read and written once
+    # by the pooling
+    P = sl.width * sl.height
+    survey_bytes = 9 * sl.n + 3 * P * (8 * D + 4)
     out["encoder_roofline"] = {
         "algorithmic_bytes": int(sum(ab[k] for k in ab if k != "gather")),
         "ms": encoder_ms,
         "frac_of_hbm": (sum(ab[k] for k in ab if k != "gather") / (encoder_ms * 1e-3) / 1e9)
-        / pk["hbm_gbs"] if encoder_ms > 0 else None}
+        / pk["hbm_gbs"] if encoder_ms > 0 else None,
+        "survey_model_bytes": int(survey_bytes),
+        "survey_model_frac": (survey_bytes / (encoder_ms * 1e-3) / 1e9) / pk["hbm_gbs"]
+        if encoder_ms > 0 else None}
 
     # plain FP32 form on the same slice and GPU
     if mode != vk.MLP_FP32:
@@ -543,6 +551,11 @@ def run_ours(args):
             out["stream"] = stream_leg(args, mode, stream)
         except Exception as e:  # the headline line is printed regardless
             out["stream"] = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0 and not args.no_small:
+        try:
+            out["small_slice"] = small_leg(args, mode, stream)
+        except Exception as e:  # the headline line is printed regardless
+            out["small_slice"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_sparse:
         try:
             out["sparse_k"] = sparse_leg(args, mode, stream)
@@ -621,6 +634,58 @@ def stream_leg(args, mode, stream):
            "flows_per_s": n_steady / (float(steady.sum()) * 1e-3), "unit": UNIT,
            "resident": "64-bit fixed-point per-pixel sums (exact add/expire) + counts"}
     st.close()
+    enc.close()
+    return res
+
+
+def small_leg(args, mode, stream):
+    """The small single-slice case: 346x260, 20,000 events over 10 ms (D = 64,
+    21x21 window), every event requested; the chosen mode and the plain FP32
+    form, per call with the inputs resident (p50 and p99 over the timed calls),
+    and the flows' error against the FP64 oracle on every event."""
+    import torch
+    import oracle
+    from paper_2504_19417_gb300 import synth
+    from paper_2504_19417_gb300 import veckm as vk
+    sl, D = synth.workload("slice-346x260-20k")
+    T, X, Y = synth.frequencies(D, 0)
+    w = synth.mlp_weights(D, 128, 3)
+    p = vk.Params(width=sl.width, height=sl.height, D=D, dx=10, dy=10, dt_us=16_000,
+                  t_span_us=int(sl.t.max()) - sl.t_ref)
+    enc = vk.Encoder(p, w.W1, w.b1, w.W2, w.b2, T, X, Y, mlp_mode=mode)
+    enc.autotune(sl.width, sl.height, stream)
+    x = torch.from_numpy(sl.x).cuda()
+    y = torch.from_numpy(sl.y).cuda()
+    t = torch.from_numpy(sl.t.view(np.int32)).cuda()
+    flow = torch.empty((sl.n, 2), dtype=torch.float32, device="cuda")
+    e = oracle.encode_pooled(sl.x, sl.y, sl.t, sl.t_ref, sl.width, sl.height, D, 10, 10, 16_000.0,
+                             T, X, Y)[0]
+    fref = oracle.mlp(e, w.W1, w.b1, w.W2, w.b2)
+    nref = np.linalg.norm(fref, axis=1)
+    floor = 0.25 * np.median(nref)
+    res = {"workload": f"slice-346x260-20k ({sl.n} events, 10 ms, D={D}, 21x21)"}
+    for name, m in ((args.mode, mode), ("fp32", vk.MLP_FP32)):
+        enc.set_mlp_mode(m)
+        for _ in range(args.warmup):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+        k = max(10, args.steps)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for i in range(k):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+            evs[i + 1].record(stream)
+        evs[-1].synchronize()
+        per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(k)])
+        f = flow.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(f - fref, axis=1) / np.maximum(nref, floor)
+        res[name] = {"flows_per_s": sl.n / (float(per.mean()) * 1e-3),
+                     "ms_per_call": float(per.mean()), "p50_ms": float(np.percentile(per, 50)),
+                     "p99_ms": float(np.percentile(per, 99)),
+                     "kernels_per_call": enc.last_launch_count(),
+                     "flow_rel_max": float(rel.max()), "flow_rel_mean": float(rel.mean()),
+                     "flow_rel_floor": "0.25 x median |flow|"}
+    enc.sync_status()
     enc.close()
     return res
 
@@ -1228,6 +1293,7 @@ def main():
     ap.add_argument("--precision-sample", type=int, default=5_000)
     ap.add_argument("--no-autotune", action="store_true", help="default pooling launch shapes")
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-request leg")
+    ap.add_argument("--no-small", action="store_true", help="skip the 346x260 20k-event leg")
     ap.add_argument("--no-stream", action="store_true", help="skip the sliding-window leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-rates", default="1000,2000,4000,6000,8000,12000,16000",

@@ -477,6 +477,20 @@ veckm_status veckm_set_injection(veckm_ctx *ctx, int32_t what);
  * allocations counted since the previous call.  Process wide. */
 int64_t veckm_debug_fail_alloc(int64_t fail_at);
 
+/* Bounds-checked build (no counterpart in the paper; a stand-in for a device
+ * memory checker).  The library built with -DVECKM_CHECKED
+ * (paper_2504_19417_gb300/build.py, build(checked=True):
+ * libveckm_checked.so) tests every index its kernels derive from data before
+ * the access it guards (the pixel of a sorted record, a slot from an atomic
+ * counter, a bucket from an event, a ring position) and, where one would
+ * leave its buffer, counts it and skips the access.  veckm_debug_checks waits
+ * for the device (cudaDeviceSynchronize), stores the number counted since the
+ * previous call in *violations and where the first one was in *first_line
+ * (file number * 100000 + source line; files: 1 kernels.cu, 2 mlp_tc.cu,
+ * 3 stream.cu; 0 if none), and clears both.  Process wide.  In the normal
+ * build it returns VECKM_EUNSUPPORTED and the checks compile away. */
+veckm_status veckm_debug_checks(int64_t *violations, int32_t *first_line);
+
 /* SplitMix64 + Box-Muller standard normals (the generator behind freq_seed):
  * writes count normals of stream `seed` to h_out.  Host only. */
 void veckm_normals(uint64_t seed, int64_t count, double *h_out);

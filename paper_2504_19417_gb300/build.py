@@ -2,6 +2,8 @@
 
 Each .cu file under csrc/ is compiled to an object in parallel, then the
 objects are linked into ``paper_2504_19417_gb300/_lib/libveckm.so``.
+``build(checked=True)`` builds the same sources with device-side bounds
+checks (-DVECKM_CHECKED) into ``_lib/checked/libveckm_checked.so``.
 Nothing is installed outside the repository.
 """
 from __future__ import annotations
@@ -18,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libveckm.so")
+CHECKED_DIR = os.path.join(OUT_DIR, "checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libveckm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -46,20 +50,23 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if sources changed) and return the path of libveckm.so."""
-    stamp = _stamp()
-    stamp_file = LIB + ".stamp"
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile (if sources changed) and return the path of libveckm.so (or, with
+    checked=True, of the bounds-checked libveckm_checked.so)."""
+    lib_path, out_dir = (CHECKED_LIB, CHECKED_DIR) if checked else (LIB, OUT_DIR)
+    flags = [*FLAGS, *extra_flags] + (["-DVECKM_CHECKED"] if checked else [])
+    stamp = _stamp() + ("+checked" if checked else "")
+    stamp_file = lib_path + ".stamp"
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp_file):
         with open(stamp_file) as f:
             if f.read().strip() == stamp:
-                return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+                return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
     for src in _sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -73,17 +80,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(out.decode(errors="replace"), file=sys.stderr)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(f"{s}:\n{o}" for s, o in failed))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra_flags=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else []))
+                extra_flags=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else [],
+                checked="--checked" in sys.argv))

@@ -46,6 +46,7 @@
 
 #include <algorithm>
 
+#include "check.cuh"
 #include "phase.cuh"
 #include "veckm_internal.h"
 
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__res
       if (key[e] >= 0) pos[e] = atomicAdd(cur + key[e], 1);
 #pragma unroll
     for (int e = 0; e < kPlaceILP; ++e)
-      if (key[e] >= 0) {
+      if (key[e] >= 0 && VK_CHECK(pos[e] >= 0 && pos[e] < ev.n)) {
         rec[pos[e]] = make_int2((int)tr[e], (int)(k0 + e * stride));
         pix[pos[e]] = key[e];
       }
@@ -354,7 +355,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geo
       if (j >= te.m) continue;
       uint32_t trel;
       if (event_ok(x[e], y[e], t[e], ev, g.W, g.H, trel)) {
-        atomicAdd(&h[(y[e] * g.W + x[e]) >> shift], 1);
+        const int b = (y[e] * g.W + x[e]) >> shift;
+        if (VK_CHECK(b < nb)) atomicAdd(&h[b], 1);
       } else {
         atomicOr(err, ERR_EVENT_RANGE);
         if (zero_flow)
@@ -435,6 +437,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_scatter(Events ev, G
       uint32_t trel;
       if (j < te.m && event_ok(x[e], y[e], t[e], ev, g.W, g.H, trel)) {
         const int p = y[e] * g.W + x[e];
+        if (!VK_CHECK((p >> shift) < nb)) continue;
         const int d = atomicAdd(&fil[p >> shift], 1);
         if (d < per_tile) {  // always, when the counts came from the same events
           st_t[d] = (int)trel;
@@ -451,7 +454,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_scatter(Events ev, G
     const int p = st_p[d];
     const int b = p >> shift;
     if (p < 0 || b >= nb) continue;
-    brec[cur[b] + (d - loc[b])] = make_int4(st_t[d], st_k[d], p, 0);
+    const int64_t q = (int64_t)cur[b] + (d - loc[b]);
+    if (VK_CHECK(q >= 0 && q < ev.n)) brec[q] = make_int4(st_t[d], st_k[d], p, 0);
   }
 }
 
@@ -644,6 +648,7 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
 #pragma unroll
     for (int v = 0; v < DV; ++v) s[v] = f4zero();
     auto write = [&](bool shared) {
+      if (!VK_CHECK(sp >= 0 && (int64_t)sp < (int64_t)g.W * g.H)) return;
       float4 *dst = acc + (size_t)sp * U + lane;
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
@@ -1066,7 +1071,8 @@ __global__ void __launch_bounds__(256) k_predict_fp32(Events ev, const int64_t *
       if (i < ns) {
         if (rec) {
           const int2 r = __ldg(rec + i);
-          const int p = __ldg(rpix + i);
+          int p = __ldg(rpix + i);
+          if (!VK_CHECK(p >= 0 && (int64_t)p < (int64_t)g.W * g.H)) p = 0;
           const float inv = 1.0f / (float)__ldg(ncnt + p);
 #pragma unroll
           for (int v = 0; v < DV; ++v) {
@@ -1672,5 +1678,7 @@ int launch_predict_fp32(const Events &ev, const int64_t *K, int64_t nK, const in
   VECKM_DISPATCH_DV(g.U, (predict_fp32_impl<DV>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled,
                                                 ncnt, mlp, flow, err, s)));
 }
+
+VK_CHECK_READER(check_read_kernels)
 
 }  // namespace veckm

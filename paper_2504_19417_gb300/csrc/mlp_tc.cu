@@ -54,6 +54,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "check.cuh"
 #include "phase.cuh"
 #include "veckm_internal.h"
 
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(Shape<DV>::threads, 1)
       if (rec) {
         const int2 r = __ldg(rec + i);
         pix = __ldg(rpix + i);
+        if (!VK_CHECK(pix >= 0 && (int64_t)pix < (int64_t)g.W * g.H)) pix = 0;
         trel = (uint32_t)r.x;
         outk = r.y;
         inv = 1.f;
@@ -911,6 +913,7 @@ __global__ void __launch_bounds__(TmShape<P>::threads, 1)
       if (rec) {
         const int2 r = __ldg(rec + i);
         pix = __ldg(rpix + i);
+        if (!VK_CHECK(pix >= 0 && (int64_t)pix < (int64_t)g.W * g.H)) pix = 0;
         trel = (uint32_t)r.x;
         outk = r.y;
         inv = 1.f;
@@ -1265,5 +1268,7 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
 #undef VECKM_TC
 #undef VECKM_TM
 }
+
+VK_CHECK_READER(check_read_head)
 
 }  // namespace veckm

@@ -40,6 +40,7 @@
 #include <new>
 
 #include "ctx.h"
+#include "check.cuh"
 #include "phase.cuh"
 
 namespace veckm {
@@ -198,7 +199,7 @@ template <int DV>
 __global__ void __launch_bounds__(256)
     k_ring_apply(const RingState *st, int sign,
                  const int16_t *__restrict__ rx, const int16_t *__restrict__ ry,
-                 const uint32_t *__restrict__ rt, long long cap, int W, int U,
+                 const uint32_t *__restrict__ rt, long long cap, int W, int U, long long npx,
                  const uint2 *__restrict__ wt, long long *__restrict__ acc64,
                  int *__restrict__ cnt, uint8_t *__restrict__ dirty) {
   const int lane = threadIdx.x & 31;
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(256)
        j += nw) {
     const long long pos = (first + j) % cap;
     const int p = ry[pos] * W + rx[pos];
+    if (!VK_CHECK(p >= 0 && p < npx)) continue;  // the ring holds on-sensor events only
     const uint32_t t = rt[pos];
     long long *dst = acc64 + (size_t)p * 4 * U;
 #pragma unroll
@@ -304,6 +306,8 @@ __global__ void __launch_bounds__(256) k_fixed_to_float_dirty(const long long *_
 }
 
 }  // namespace
+VK_CHECK_READER(check_read_stream)
+
 }  // namespace veckm
 
 using namespace veckm;
@@ -392,10 +396,10 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   auto apply = [&](int sign) {
     const int blocks = num_sms() * 8;
     switch (DV) {
-      case 1: k_ring_apply<1><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
-      case 2: k_ring_apply<2><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
-      case 3: k_ring_apply<3><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
-      default: k_ring_apply<4><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, c->wt, s->acc64, s->cnt, s->dirty); break;
+      case 1: k_ring_apply<1><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
+      case 2: k_ring_apply<2><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
+      case 3: k_ring_apply<3><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
+      default: k_ring_apply<4><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
     }
   };
   int launches = 0;

@@ -647,6 +647,32 @@ int64_t veckm_debug_fail_alloc(int64_t fail_at) {
   return n;
 }
 
+veckm_status veckm_debug_checks(int64_t *violations, int32_t *first_line) {
+#ifndef VECKM_CHECKED
+  (void)violations;
+  (void)first_line;
+  return fail(VECKM_EUNSUPPORTED, "not the bounds-checked build (build(checked=True))");
+#else
+  if (!violations || !first_line) return fail(VECKM_EINVAL, "null output");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "waiting for the device");
+  int (*readers[])(int *) = {veckm::check_read_kernels, veckm::check_read_head,
+                             veckm::check_read_stream};
+  int64_t total = 0;
+  int32_t first = 0;
+  for (int f = 0; f < 3; ++f) {
+    int line = 0;
+    const int n = readers[f](&line);
+    if (n < 0) return cuda_fail(cudaGetLastError(), "reading the check words");
+    if (n > 0 && first == 0) first = (f + 1) * 100000 + line;
+    total += n;
+  }
+  *violations = total;
+  *first_line = first;
+  return VECKM_OK;
+#endif
+}
+
 veckm_status veckm_set_wait_limit(veckm_ctx *c, int64_t cycles) {
   if (!c) return fail(VECKM_EINVAL, "null context");
   if (cycles < 0) return fail(VECKM_EINVAL, "negative wait limit");

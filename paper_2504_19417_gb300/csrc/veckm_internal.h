@@ -104,6 +104,13 @@ int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total
 // records (n bounds it).  Pixels without records are not written.
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
                   const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear = true);
+// Readers of the bounds-checked build's violation words, one per translation
+// unit with checks: the count since the previous read (the first source line
+// in *line), then cleared; -1 if the device could not be read; 0 in the
+// normal build.
+int check_read_kernels(int *line);
+int check_read_head(int *line);
+int check_read_stream(int *line);
 // Blocks of `threads` threads with `smem` dynamic bytes that fit on one SM.
 int blocks_per_sm(const void *func, int threads, size_t smem);
 // Pooling: row pass acc -> hbuf, column pass hbuf -> acc, window counts.

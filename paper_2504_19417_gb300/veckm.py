@@ -83,7 +83,7 @@ EXPORTS = ("veckm_create", "veckm_destroy", "veckm_encode", "veckm_encode_noallo
            "veckm_last_path", "veckm_set_path_model", "veckm_stream_create", "veckm_stream_push",
            "veckm_stream_window", "veckm_stream_accumulator", "veckm_stream_destroy",
            "veckm_set_wait_limit", "veckm_set_injection", "veckm_debug_fail_alloc",
-           "veckm_normals")
+           "veckm_debug_checks", "veckm_normals")
 INJECT_NONE, INJECT_HEAD_STALL = 0, 1
 
 
@@ -93,13 +93,23 @@ def debug_fail_alloc(fail_at: int) -> int:
     return int(lib().veckm_debug_fail_alloc(fail_at))
 
 
+def debug_checks() -> Tuple[int, int]:
+    """Bounds-checked build only: waits for the device and returns (number of
+    indices that would have left their buffer since the previous call, where
+    the first was: file number * 100000 + source line), then clears them."""
+    n, line = C.c_int64(0), C.c_int32(0)
+    _check(lib().veckm_debug_checks(C.byref(n), C.byref(line)))
+    return int(n.value), int(line.value)
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.CHECKED_LIB if os.environ.get("VECKM_LIBRARY") == "checked" else _build.LIB
 
 
 def load_library(path: Optional[str] = None) -> C.CDLL:
-    """Load libveckm.so (building it first if needed) and declare its signatures."""
-    path = path or _build.build()
+    """Load libveckm.so (building it first if needed) and declare its signatures.
+    With VECKM_LIBRARY=checked in the environment, the bounds-checked build."""
+    path = path or _build.build(checked=os.environ.get("VECKM_LIBRARY") == "checked")
     lib = C.CDLL(path)
     P, i64, u32, i32 = C.c_void_p, C.c_int64, C.c_uint32, C.c_int
     lib.veckm_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(_Config)]
@@ -125,6 +135,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.veckm_set_injection.argtypes = [P, i32]
     lib.veckm_debug_fail_alloc.argtypes = [i64]
     lib.veckm_debug_fail_alloc.restype = i64
+    lib.veckm_debug_checks.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    lib.veckm_debug_checks.restype = C.c_int
     lib.veckm_normals.argtypes = [C.c_uint64, i64, P]
     lib.veckm_normals.restype = None
     i32 = C.c_int32

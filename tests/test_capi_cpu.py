@@ -31,6 +31,13 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(vk.EXPORTS)
 
 
+def test_checks_reader_is_refused_by_the_normal_build():
+    # the bounds-checked build is a separate library; this one has no checks
+    with pytest.raises(vk.VeckmError) as ei:
+        vk.debug_checks()
+    assert ei.value.status == vk.VECKM_EUNSUPPORTED
+
+
 def test_normals_match_generator():
     for seed in (0, 1, 2, 12345):
         a = vk.normals(seed, 257)
