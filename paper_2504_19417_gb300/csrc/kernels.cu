@@ -1557,13 +1557,19 @@ int bucket_sort_max_buckets() { return kMaxBuckets; }
 
 int bucket_sort_max_tiles() { return kMaxSortTiles; }
 
-// events per tile: one round of the block, or two for inputs that would
-// need more than kMaxSortTiles tiles; 0 when even that is too many
+// events per tile: from one to two rounds of the block, as many as fill one
+// wave of the scatter, and two for inputs that would need more than
+// kMaxSortTiles tiles; 0 when even that is too many
 static int64_t bucket_sort_tile(int64_t n) {
   const int64_t one = (int64_t)kSortILP * kSortThreads;
-  if (n <= one * kMaxSortTiles) return one;
-  if (n <= 2 * one * kMaxSortTiles) return 2 * one;
-  return 0;
+  if (n > 2 * one * kMaxSortTiles) return 0;
+  // the fewest events per tile (a multiple of 512, from one to two rounds of
+  // the block) that leave no second wave of the scatter (three blocks per SM)
+  const int64_t slots = 3 * (int64_t)num_sms();
+  int64_t t = (n + slots - 1) / slots;
+  t = std::max(one, std::min(2 * one, (t + 511) / 512 * 512));
+  if ((n + t - 1) / t > kMaxSortTiles) t = 2 * one;
+  return t;
 }
 
 bool bucket_sort_fits(int64_t P, int64_t n) {
