@@ -642,7 +642,8 @@ def small_leg(args, mode, stream):
     """The small single-slice case: 346x260, 20,000 events over 10 ms (D = 64,
     21x21 window), every event requested; the chosen mode and the plain FP32
     form, per call with the inputs resident (p50 and p99 over the timed calls),
-    and the flows' error against the FP64 oracle on every event."""
+    the chosen mode also as a one-slice captured plan, and the flows' error
+    against the FP64 oracle on every event."""
     import torch
     import oracle
     from paper_2504_19417_gb300 import synth
@@ -685,6 +686,30 @@ def small_leg(args, mode, stream):
                      "kernels_per_call": enc.last_launch_count(),
                      "flow_rel_max": float(rel.max()), "flow_rel_mean": float(rel.mean()),
                      "flow_rel_floor": "0.25 x median |flow|"}
+    # the same slice as a one-slice plan: the whole call captured in a CUDA
+    # graph and replayed (launch overhead paid once per replay, not per kernel)
+    enc.set_mlp_mode(mode)
+    plan = enc.plan([vk.Slice(x, y, t, sl.t_ref, sl.width, sl.height)], out=flow)
+    for _ in range(args.warmup):
+        plan.launch(stream)
+    k = max(10, args.steps)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(k):
+        plan.launch(stream)
+        evs[i + 1].record(stream)
+    evs[-1].synchronize()
+    per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(k)])
+    f = flow.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(f - fref, axis=1) / np.maximum(nref, floor)
+    res[args.mode + "_plan"] = {"flows_per_s": sl.n / (float(per.mean()) * 1e-3),
+                                "ms_per_call": float(per.mean()),
+                                "p50_ms": float(np.percentile(per, 50)),
+                                "p99_ms": float(np.percentile(per, 99)),
+                                "kernels_per_call": plan.kernel_count,
+                                "flow_rel_max": float(rel.max())}
+    plan.close()
     enc.sync_status()
     enc.close()
     return res
