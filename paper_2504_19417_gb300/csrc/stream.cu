@@ -24,8 +24,8 @@
 //   1. flag the packet's valid events (inside the sensor and the window, not
 //      earlier than an event accepted before them) and scan the flags: the
 //      valid events' places in the ring;
-//   2. find the first ring event still in the window (binary search) and how
-//      many valid events fit the ring after the expiry;
+//   2. find the first ring event still in the window (a 32-way search by one
+//      warp) and how many valid events fit the ring after the expiry;
 //   3. subtract the events that left;
 //   4. append the valid events that fit (K[i] = an event's ring slot, or -1:
 //      its output row is zeroed and the error word set);
@@ -178,18 +178,33 @@ __global__ void __launch_bounds__(kMaxThreads) k_tmax_order(const unsigned *__re
 __global__ void k_ring_tail(RingState *st, const uint32_t *__restrict__ rt, long long cap,
                             uint32_t t_lo, const int *__restrict__ nvalid) {
   const long long n = nvalid ? *nvalid : 0;
-  if (threadIdx.x != 0) return;
-  long long lo = st->tail, hi = st->head;
-  st->tail_old = lo;
+  const int lane = threadIdx.x & 31;
+  const long long head = st->head, tail0 = st->tail;
+  long long lo = tail0, hi = head;
+  // 32-way search with the warp: lane j probes lo + j * step; the first
+  // probe at or after t_lo bounds the answer (the ring's times ascend) to
+  // the step before it, so each round divides the range by 32
   while (lo < hi) {
-    const long long mid = lo + (hi - lo) / 2;
-    if (rt[mid % cap] < t_lo) lo = mid + 1;
-    else hi = mid;
+    const long long step = (hi - lo + 31) / 32;
+    const long long pos = lo + (long long)lane * step;
+    const bool ge = pos >= hi || rt[pos % cap] >= t_lo;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    if (m == 0) {  // every probe before t_lo (all 32 inside the range)
+      lo += 31 * step + 1;
+      continue;
+    }
+    const int f = __ffs(m) - 1;
+    const long long nhi = lo + (long long)f * step < hi ? lo + (long long)f * step : hi;
+    if (f > 0) lo += (long long)(f - 1) * step + 1;
+    hi = nhi;
   }
-  st->tail = lo;
-  st->head_old = st->head;
-  const long long room = cap - (st->head - lo);
-  st->app = n < room ? n : room;
+  if (lane == 0) {
+    st->tail_old = tail0;
+    st->tail = lo;
+    st->head_old = head;
+    const long long room = cap - (head - lo);
+    st->app = n < room ? n : room;
+  }
 }
 
 // 3./5. subtract (sign -1: ring events [tail_old, tail)) or add (+1: the
