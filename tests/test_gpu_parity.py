@@ -90,7 +90,7 @@ MODES = [vk.MLP_FP32, vk.MLP_FP16, vk.MLP_BF16, vk.MLP_FP16 | vk.ACC_FP16,
 
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("W,H,n,D", [(346, 260, 20_000, 64), (150, 100, 6_000, 128),
-                                     (90, 70, 333, 64)])
+                                     (90, 70, 333, 64), (60, 40, 97, 128)])
 def test_predict_matches_oracle(mode, W, H, n, D):
     sl = synth.event_slice(W, H, n, 10_000, n_edges=8, seed=n + D)
     enc, TXY, w = make(sl, D, mode=mode)
@@ -98,6 +98,23 @@ def test_predict_matches_oracle(mode, W, H, n, D):
     flow = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
     enc.sync_status()
     _check_flow(flow, _oracle_emb(sl, D, 10, 10, 16_000, TXY), w, mode)
+
+
+@pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_BF16 | vk.ACC_FP16])
+def test_explicit_requests_d128(mode):
+    """D = 128 with an explicit request list (rows in request order, repeats,
+    a ragged last tile): each row equals the full call's row and the oracle."""
+    sl = synth.event_slice(200, 150, 12_000, 10_000, n_edges=6, seed=131)
+    enc, TXY, w = make(sl, 128, mode=mode)
+    x, y, t = to_dev(sl)
+    full = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+    rng = np.random.default_rng(13)
+    K = rng.choice(sl.n, 1_000 + 37, replace=True).astype(np.int64)
+    fk = enc.predict(x, y, t, sl.t_ref, K=torch.from_numpy(K).cuda()).cpu().numpy()
+    enc.sync_status()
+    ref = _oracle_emb(sl, 128, 10, 10, 16_000, TXY, K=K)
+    _check_flow(fk, ref, w, mode)
+    assert np.allclose(fk, full[K], rtol=0, atol=1e-3 * (1 + np.abs(full).max()))
 
 
 @pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_FP16 | vk.ACC_FP16])
