@@ -24,16 +24,7 @@
 namespace veckm {
 namespace {
 
-// One slice as the mapping kernel sees it.
-struct SliceDev {
-  const int16_t *x, *y;
-  const uint32_t *t;
-  long long n;    // events
-  long long off;  // first canvas event (sum of the previous slices' n)
-  long long blk;  // first block of the mapping kernel
-  uint32_t t_ref;
-  int W, H, ox, oy;
-};
+using SliceDev = CanvasSlice;  // one slice as the mapping kernel sees it
 
 constexpr int kMapThreads = 256;
 constexpr int kMapPer = 4;  // events per thread
@@ -198,7 +189,11 @@ veckm_status launch_map(veckm_ctx *c, const Prepared &p, cudaStream_t s) {
 veckm_status run_canvas(veckm_ctx *c, const Prepared &p, float *out, bool flow, cudaStream_t s) {
   if (veckm_status st = launch_map(c, p, s)) return st;
   const Events ev{c->cx, c->cy, c->ct, p.N, 0u, (uint32_t)c->t_span};
-  veckm_status st = run_pipeline(c, p.g, ev, nullptr, p.N, out, flow, s, c->tune_for(p.g));
+  // the pooling passes skip what lies away from every slice (canvas gaps)
+  Geometry g = p.g;
+  g.canvas = static_cast<const SliceDev *>(c->slice_tab);
+  g.ncanvas = (int)p.tab.size();
+  veckm_status st = run_pipeline(c, g, ev, nullptr, p.N, out, flow, s, c->tune_for(p.g));
   if (st == VECKM_OK && p.blocks > 0) c->last_launches += 1;
   return st;
 }

@@ -753,6 +753,23 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   const int o0 = s * seg;
   const int nout = min(len, o0 + seg) - o0;
   const int in0 = o0 - r;
+  if (g.ncanvas > 0) {
+    // a batch's canvas: only outputs some slice depends on are computed.  The
+    // column pass's outputs inside a slice; the row pass's outputs in a
+    // slice's columns within dy rows of it (what those column windows read).
+    // Every window of a needed output reads needed values only, and van Herk
+    // sums never mix in values from outside a window.
+    bool need = false;
+    for (int i = lane; i < g.ncanvas; i += 32) {
+      const CanvasSlice &cs = g.canvas[i];
+      if (P == Pass::Rows)
+        need |= line >= cs.oy - g.dy && line < cs.oy + cs.H + g.dy && o0 < cs.ox + cs.W &&
+                o0 + nout > cs.ox;
+      else
+        need |= line >= cs.ox && line < cs.ox + cs.W && o0 < cs.oy + cs.H && o0 + nout > cs.oy;
+    }
+    if (!__any_sync(kFull, need)) return;
+  }
   // this warp's slice of each pixel: units u0 .. u0 + U - 1 of up (grids and
   // tables are [pixel][up] units; the ring holds one slice)
   const int u0 = blockIdx.y * U;

@@ -22,8 +22,25 @@ struct Events {
 // Device-side constant state of a context.  Complex values are stored as
 // interleaved (re, im) FP32 with the channel index fastest; one float4 holds
 // channels 2u and 2u+1 ("unit" u), so a pixel has U = D/2 units.
+// One slice of a batch as it sits on the canvas (batch.cu): its events, its
+// place among the canvas events and the mapping kernel's blocks, and its
+// sensor's size and offset on the canvas.
+struct CanvasSlice {
+  const int16_t *x, *y;
+  const uint32_t *t;
+  long long n;    // events
+  long long off;  // first canvas event (sum of the previous slices' n)
+  long long blk;  // first block of the mapping kernel
+  uint32_t t_ref;
+  int W, H, ox, oy;
+};
+
 struct Geometry {
   int W, H, D, U, dx, dy;
+  // a batch's canvas (device table of its slices, or null): the pooling
+  // passes skip line segments that no slice's outputs depend on
+  const CanvasSlice *canvas = nullptr;
+  int ncanvas = 0;
 };
 
 struct Tables {
