@@ -46,6 +46,7 @@
 
 #include <algorithm>
 
+#include "chain.cuh"
 #include "check.cuh"
 #include "phase.cuh"
 #include "veckm_internal.h"
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geo
                                                                   int *__restrict__ err,
                                                                   float *__restrict__ zero_flow) {
   __shared__ int h[kMaxBuckets];
+  chain_release();  // the scan may launch now
   for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const TileEvents te(ev, per_tile);
@@ -374,6 +376,8 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const int *__restrict__ bh
                                                       int tiles, int *__restrict__ bpre,
                                                       int *__restrict__ btot) {
   __shared__ int s_warp[33];
+  chain_wait();
+  chain_release();
   const int b = blockIdx.x;
   const int i0 = 4 * threadIdx.x;
   int c[4], v = 0;
@@ -406,6 +410,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_scatter(Events ev, G
   __shared__ int loc[kMaxBuckets];  // offset of each bucket's run within the tile
   __shared__ int fil[kMaxBuckets];  // fill cursor of each run
   __shared__ int s_warp[33];
+  chain_wait();
+  chain_release();
   const int *cnt_tile = bhist + (size_t)blockIdx.x * nb;
   block_scan_small(btot, nb, cur, nullptr, s_warp);  // bucket bases
   int nvalid;
@@ -478,6 +484,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_sort(const int4 *__r
   int *st_r = st_p + kSortStage, *src = st_r;  // ranks, then (reused) sources
   __shared__ int s_warp[33];
   __shared__ int s_base[2];
+  chain_wait();
+  chain_release();
   const int b = blockIdx.x;
   const int64_t p0 = (int64_t)b << shift;
   // this bucket's first record: the sum of the earlier buckets' totals
@@ -633,6 +641,8 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
                                                 const int2 *__restrict__ rec,
                                                 const int *__restrict__ rpix,
                                                 float4 *__restrict__ acc, int recs) {
+  chain_wait();
+  chain_release();
   constexpr int U = 32 * DV;
   const int lane = threadIdx.x & 31;
   const int64_t ns = *nsorted;
@@ -734,6 +744,8 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
                                                  const int *__restrict__ ncnt = nullptr,
                                                  const int *__restrict__ occ = nullptr) {
   static_assert(EMIT == kEmitF32 || P == Pass::Cols, "normalised output: column pass only");
+  chain_wait();
+  chain_release();
   constexpr bool HALF = EMIT == kEmitF16N;
   constexpr bool NORM = HALF;  // divided by the window counts
   constexpr int U = 32 * DV;
@@ -1405,7 +1417,8 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 
 template <int DV>
 int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear) {
+                const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear,
+                bool chain) {
   const int64_t P = (int64_t)g.W * g.H;
   if (clear && cudaMemsetAsync(acc, 0, (size_t)P * g.U * sizeof(float4), s) != cudaSuccess)
     return -1;
@@ -1413,8 +1426,11 @@ int pixsum_impl(const Geometry &g, const Tables &tb, const int *nsorted, const i
   const int64_t recs = kPixRecs;
   const int64_t warps = (n + recs - 1) / recs;
   const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
-  k_pixsum<DV><<<grid, 256, 0, s>>>(g, tb, nsorted, rec, rpix, acc, (int)recs);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  // after a clear the memset, not a kernel, comes before the launch
+  return launch_kernel(k_pixsum<DV>, dim3(grid), dim3(256), 0, s, chain && !clear, g, tb, nsorted,
+                       rec, rpix, acc, (int)recs) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 // Largest dynamic shared memory a box-pass block may ask for.
@@ -1422,7 +1438,8 @@ constexpr size_t kBoxSmemMax = 200 * 1024;
 
 template <int DV, Pass P, int EMIT = kEmitF32>
 int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst, cudaStream_t s,
-             const int *ncnt, int seg_windows, int wpb_req, const int *occ = nullptr) {
+             const int *ncnt, int seg_windows, int wpb_req, const int *occ = nullptr,
+             bool chain = false) {
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
   const int L = 2 * r + 1;
   const int len = (P == Pass::Rows) ? g.W : g.H;
@@ -1439,9 +1456,10 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   if (set_smem(k_box_pass<1, P, EMIT>, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const dim3 grid((unsigned)((warps + wpb - 1) / wpb), DV);
-  k_box_pass<1, P, EMIT><<<grid, 32 * wpb, sm, s>>>(src, dst, g, tb, seg, nseg, 32 * DV, ncnt,
-                                                    occ);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_kernel(k_box_pass<1, P, EMIT>, grid, dim3(32 * wpb), sm, s, chain, src, dst, g, tb,
+                       seg, nseg, 32 * DV, ncnt, occ) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 template <int DV>
@@ -1619,19 +1637,23 @@ int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total
                                                zero_flow);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   int *bpre = bhist + (size_t)nb * tiles;
-  k_bucket_scan<<<nb, scan_threads, 0, s>>>(bhist, nb, tiles, bpre, btot);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_bucket_scatter<<<tiles, kSortThreads, scatter_sm, s>>>(ev, g, shift, nb, (int)per_tile, bhist,
-                                                          bpre, btot, brec);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_bucket_sort<<<nb, kSortThreads, sort_sm, s>>>(brec, shift, nb, P, btot, cnt, total, rec, rpix,
-                                                  zgrid, g.U);
-  return cudaPeekAtLastError() == cudaSuccess ? 4 : -1;
+  // the other three are chained to the kernel before them
+  if (launch_kernel(k_bucket_scan, dim3(nb), dim3(scan_threads), 0, s, true, bhist, nb, tiles,
+                    bpre, btot) != cudaSuccess)
+    return -1;
+  if (launch_kernel(k_bucket_scatter, dim3(tiles), dim3(kSortThreads), scatter_sm, s, true, ev, g,
+                    shift, nb, (int)per_tile, bhist, bpre, btot, brec) != cudaSuccess)
+    return -1;
+  return launch_kernel(k_bucket_sort, dim3(nb), dim3(kSortThreads), sort_sm, s, true, brec, shift,
+                       nb, P, btot, cnt, total, rec, rpix, zgrid, g.U) == cudaSuccess
+             ? 4
+             : -1;
 }
 
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear) {
-  VECKM_DISPATCH_DV(g.U, (pixsum_impl<DV>(g, tb, nsorted, rec, rpix, n, acc, s, clear)));
+                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear,
+                  bool chain) {
+  VECKM_DISPATCH_DV(g.U, (pixsum_impl<DV>(g, tb, nsorted, rec, rpix, n, acc, s, clear, chain)));
 }
 
 int launch_pixsum_owned(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
@@ -1650,10 +1672,10 @@ int launch_direct(const Events &ev, const int64_t *K, int64_t nK, const Geometry
 }
 
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
-                     cudaStream_t s, const Tune &tn, const int *occ) {
+                     cudaStream_t s, const Tune &tn, const int *occ, bool chain) {
   if (occ && 2 * g.dx + 1 > 32) return -1;  // the occupancy mask covers one warp's lanes
   VECKM_DISPATCH_DV(g.U, (box_pass<DV, Pass::Rows>(g, tb, acc, hbuf, s, nullptr, tn.rows_seg,
-                                                   tn.rows_wpb, occ)));
+                                                   tn.rows_wpb, occ, chain)));
 }
 
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,

@@ -50,6 +50,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "chain.cuh"
 #include "check.cuh"
 #include "phase.cuh"
 #include "veckm_internal.h"
@@ -339,6 +340,9 @@ __global__ void __launch_bounds__(TmShape<P, S>::threads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  // the prologue above reads only the weights; the step's grids, records and
+  // outputs from here on
+  chain_wait();
   const int ns = rec ? *nsorted : (int)nK;
   const int ntiles_all = (int)((nK + kM - 1) / kM);
   const int nlocal = (int)blockIdx.x < ntiles_all
@@ -668,7 +672,8 @@ template <int DV, bool HALF, bool F16>
 int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *rec,
                     const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                     const void *pooled, const int *ncnt, const MLP &mlp, float *flow, int *err,
-                    cudaStream_t s, float4 *zero_buf, int64_t zero_units, bool *zeroed) {
+                    cudaStream_t s, float4 *zero_buf, int64_t zero_units, bool *zeroed,
+                    bool chain) {
   if (zeroed) *zeroed = false;
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
@@ -694,10 +699,10 @@ int predict_tm_impl(const Events &ev, const int64_t *K, int64_t nK, const int2 *
   for (int u = 0; u < 32 * DV; ++u)
     ep.wt[u] = make_uint4(mlp.hwt[2 * u].x, mlp.hwt[2 * u].y, mlp.hwt[2 * u + 1].x,
                           mlp.hwt[2 * u + 1].y);
-  kern<<<grid, TmShape<P, S>::threads, sm, s>>>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled,
-                                                ncnt, mlp, flow, err, zero ? zero_buf : nullptr,
-                                                zero ? zero_units : 0, ep);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (launch_kernel(kern, dim3(grid), dim3(TmShape<P, S>::threads), sm, s, chain, ev, K, nK, rec,
+                    rpix, nsorted, g, tb, pooled, ncnt, mlp, flow, err,
+                    zero ? zero_buf : nullptr, zero ? zero_units : 0, ep) != cudaSuccess)
+    return -1;
   if (zeroed) *zeroed = zero;
   return 1;
 }
@@ -708,12 +713,12 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
                       const int *rpix, const int *nsorted, const Geometry &g, const Tables &tb,
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
                       int *err, cudaStream_t s, const Tune &tn, float4 *zero_buf,
-                      int64_t zero_units, bool *zeroed) {
+                      int64_t zero_units, bool *zeroed, bool chain) {
   (void)tn;
   const bool h = mlp.pooled_half != 0, f16 = mlp.half_kind != 0;
 #define VECKM_TM(DV_, H_, F_)                                                                \
   predict_tm_impl<DV_, H_, F_>(ev, K, nK, rec, rpix, nsorted, g, tb, pooled, ncnt, mlp, flow,  \
-                               err, s, zero_buf, zero_units, zeroed)
+                               err, s, zero_buf, zero_units, zeroed, chain)
 #define VECKM_TM4(DV_)                                                                       \
   (h ? (f16 ? VECKM_TM(DV_, true, true) : VECKM_TM(DV_, true, false))                        \
      : (f16 ? VECKM_TM(DV_, false, true) : VECKM_TM(DV_, false, false)))

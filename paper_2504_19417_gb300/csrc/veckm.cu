@@ -381,12 +381,20 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     c->last_launches = launches;
     return VECKM_OK;
   }
+  // Launches that follow a kernel of this step in s, with no event wait
+  // between them, are chained to it (programmatic dependent launch): the
+  // pixel sums to the bucket sort, the row pass to the pixel sums, the head
+  // to the column pass.  The column pass follows the join with the side
+  // stream and is launched in full order.
+  const bool chain_sums = bucketed && !zjoin.armed;
   zjoin.wait();  // the clear of gsum (side stream)
-  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, false)) < 0)
+  if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, false, chain_sums)) < 0)
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
+  const bool chain_rows = r > 0;
   mark();
-  if ((r = launch_pool_rows(g, tb, gsum, grow, s, tn, sparse_rows ? c->cnt : nullptr)) < 0)
+  if ((r = launch_pool_rows(g, tb, gsum, grow, s, tn, sparse_rows ? c->cnt : nullptr,
+                            chain_rows)) < 0)
     return cuda_fail(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   mark();
@@ -415,7 +423,7 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     // a cleared grid serves only a next call whose sums cannot do without one
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
                           c->off + P, g, tb, gsum, c->ncnt, m, out, c->err, s, tn,
-                          may_zero && !sparse_rows ? grow : nullptr, units, &zeroed);
+                          may_zero && !sparse_rows ? grow : nullptr, units, &zeroed, true);
     if (r >= 0 && zeroed && !capturing) {
       c->zero_grid = grow == c->acc ? 0 : 1;
       c->zero_units = units;

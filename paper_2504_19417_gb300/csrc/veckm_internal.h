@@ -119,8 +119,12 @@ int launch_bucket_sort(const Events &ev, const Geometry &g, int *cnt, int *total
 // Clears acc (unless the caller knows it is zero, or the sort zeroed the
 // range-edge rows: clear = false), then sums the *nsorted pixel-sorted
 // records (n bounds it).  Pixels without records are not written.
+// chain (here and below): the launch may overlap the end of the kernel
+// before it in s (programmatic dependent launch, chain.cuh); only for a
+// launch whose predecessor in s is a kernel of the same step.
 int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear = true);
+                  const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool clear = true,
+                  bool chain = false);
 // Readers of the bounds-checked build's violation words, one per translation
 // unit with checks: the count since the previous read (the first source line
 // in *line), then cleared; -1 if the device could not be read; 0 in the
@@ -134,7 +138,8 @@ int blocks_per_sm(const void *func, int threads, size_t smem);
 // occ (row pass; window length 2dx+1 <= 32, else -1): per-pixel event counts,
 // pixels with none read as zero whatever acc holds there.
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,
-                     cudaStream_t s, const Tune &tn = Tune{}, const int *occ = nullptr);
+                     cudaStream_t s, const Tune &tn = Tune{}, const int *occ = nullptr,
+                     bool chain = false);
 int launch_pool_cols(const Geometry &g, const Tables &tb, const float4 *hbuf, float4 *acc,
                      cudaStream_t s, const Tune &tn = Tune{});
 int launch_counts(const Geometry &g, const int *cnt, int *cnt_tmp, int *ncnt, cudaStream_t s);
@@ -163,7 +168,7 @@ int launch_predict_tc(const Events &ev, const int64_t *K, int64_t nK, const int2
                       const void *pooled, const int *ncnt, const MLP &mlp, float *flow,
                       int *err, cudaStream_t s, const Tune &tn = Tune{},
                       float4 *zero_buf = nullptr, int64_t zero_units = 0,
-                      bool *zeroed = nullptr);
+                      bool *zeroed = nullptr, bool chain = false);
 // Forget which grid of the context is known to be zero (for paths that write
 // the grids outside the dense pipeline).
 void grids_dirty(veckm_ctx *c);
