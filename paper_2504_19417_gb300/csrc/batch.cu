@@ -186,7 +186,20 @@ veckm_status launch_map(veckm_ctx *c, const Prepared &p, cudaStream_t s) {
   return e == cudaSuccess ? VECKM_OK : fail_cuda(e, "canvas mapping launch");
 }
 
+// A batch of one slice: the layout puts it at the canvas origin and sizes the
+// canvas to it, so the canvas is that slice and its events need no mapping
+// (the pipeline applies the mapping kernel's test of sensor and time span).
+bool single_slice(const Prepared &p) {
+  return p.tab.size() == 1 && p.tab[0].ox == 0 && p.tab[0].oy == 0 && p.tab[0].W == p.g.W &&
+         p.tab[0].H == p.g.H;
+}
+
 veckm_status run_canvas(veckm_ctx *c, const Prepared &p, float *out, bool flow, cudaStream_t s) {
+  if (single_slice(p)) {
+    const SliceDev &d = p.tab[0];
+    const Events ev{d.x, d.y, d.t, d.n, d.t_ref, (uint32_t)c->t_span};
+    return run_pipeline(c, p.g, ev, nullptr, p.N, out, flow, s, c->tune_for(p.g));
+  }
   if (veckm_status st = launch_map(c, p, s)) return st;
   const Events ev{c->cx, c->cy, c->ct, p.N, 0u, (uint32_t)c->t_span};
   // the pooling passes skip what lies away from every slice (canvas gaps)
@@ -206,6 +219,7 @@ veckm_status batch_call(veckm_ctx *c, const veckm_slice *sl, int32_t ns, float *
   if (p.N == 0) return VECKM_OK;
   if (!out) return fail_msg(VECKM_EINVAL, "null output buffer");
   if (veckm_status st = reserve(c, p, s)) return st;
+  if (single_slice(p)) return run_canvas(c, p, out, flow, s);  // no slice table to upload
   const size_t bytes = p.tab.size() * sizeof(SliceDev);
   cudaError_t e = cudaSuccess;
   if (c->tab_copied) e = cudaEventSynchronize(c->tab_copied);  // the pinned copy is free again
@@ -407,7 +421,8 @@ veckm_status veckm_plan_create(veckm_ctx *c, const veckm_slice *sl, int32_t ns, 
     if (ce != cudaSuccess) {
       r = fail_cuda(ce, "stream capture");
     } else {
-      ce = cudaMemcpyAsync(c->slice_tab, pl->h_tab, bytes, cudaMemcpyHostToDevice, cs);
+      if (!single_slice(p))
+        ce = cudaMemcpyAsync(c->slice_tab, pl->h_tab, bytes, cudaMemcpyHostToDevice, cs);
       r = ce == cudaSuccess ? run_canvas(c, p, d_out, predict != 0, cs)
                             : fail_cuda(ce, "slice table copy");
       cudaGraph_t graph = nullptr;

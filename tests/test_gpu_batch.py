@@ -152,6 +152,42 @@ def test_out_of_range_event_in_a_slice_is_reported_and_zeroed():
     assert flow_rel_err(flow[keep], ref, FLOW_FLOOR).max() <= 1e-4
 
 
+def test_one_slice_batch_and_plan_read_the_slice_in_place():
+    # one slice is its own canvas: no mapping kernel, the pipeline reads the
+    # slice's buffers and applies the same test of sensor and time span
+    sls = _slices(8, [6_000], [(346, 260)])
+    sls[0].x[11] = 346              # inside the 512-wide context, outside the 346-wide sensor
+    sls[0].t[5] = sls[0].t_ref - 1  # before the slice start
+    enc, TXY, w = _ctx(512, 512)
+    dsl = _dev(sls)
+    flow = enc.predict_batch(dsl).cpu().numpy()
+    with pytest.raises(vk.VeckmError) as ei:
+        enc.sync_status()
+    assert ei.value.status == vk.VECKM_ERANGE
+    assert np.all(flow[11] == 0) and np.all(flow[5] == 0)
+    keep = np.setdiff1d(np.arange(6_000), [5, 11])
+    sub = synth.EventSlice(sls[0].x[keep], sls[0].y[keep], sls[0].t[keep], sls[0].p[keep], 346,
+                           260, sls[0].t_ref)
+    ref = oracle.mlp(_oracle(sub, TXY), w.W1, w.b1, w.W2, w.b2)
+    assert flow_rel_err(flow[keep], ref, FLOW_FLOOR).max() <= FLOW_TOL[vk.MLP_FP32]
+    launches = enc.last_launch_count()
+    plan = enc.plan(dsl)
+    assert plan.kernel_count == launches
+    got = plan.launch().cpu().numpy()
+    with pytest.raises(vk.VeckmError):
+        enc.sync_status()
+    assert np.abs(got - flow).max() <= 1e-5 * np.abs(flow).max()
+    # the plan reads the slice's buffers at each launch
+    dsl[0].y.copy_(torch.from_numpy(np.minimum(sls[0].y + 1, 259).astype(np.int16)).cuda())
+    again = plan.launch().cpu().numpy()
+    moved = enc.predict_batch(dsl).cpu().numpy()
+    assert np.abs(again - moved).max() <= 1e-5 * np.abs(moved).max()
+    assert np.abs(again - flow).max() > 1e-3
+    with pytest.raises(vk.VeckmError):
+        enc.sync_status()
+    plan.close()
+
+
 def test_batch_that_does_not_fit_the_canvas_is_refused():
     sls = _slices(6, [100] * 6, [(300, 200)] * 6)
     enc, _, _ = _ctx(640, 400)
