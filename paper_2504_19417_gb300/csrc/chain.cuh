@@ -1,17 +1,18 @@
 // Programmatic dependent launch for the kernels of one pipeline step.
 //
-// A chained launch may begin while the kernel before it in the stream is
-// still running, so that its launch and the prologue of its blocks overlap
-// the last blocks of that kernel instead of following them.
+// A chained launch is prepared while the kernel before it in the stream is
+// still running and starts as that kernel's last blocks exit, instead of
+// after its completion has gone through the stream's ordering.  No kernel
+// releases its dependents earlier (griddepcontrol.launch_dependents): blocks
+// of the next kernel resident early, waiting for this one, measured slower
+// on every workload tried.
 //
 // Device side.  chain_wait() returns once every kernel the launch depends on
 // has completed and its writes are visible; in a launch that was not chained
 // it returns at once.  Every thread of a kernel that may be chained calls it
 // before it reads or writes memory that earlier work in the stream touches:
 // the kernel then cannot complete before its predecessor, so the guarantee
-// carries down a chain.  chain_release() allows the next chained launch to
-// begin once every block of this kernel has called it or exited; the blocks
-// of that launch then wait in chain_wait() on whatever SM room is left.
+// carries down a chain.
 //
 // Host side.  launch_kernel(kern, grid, block, smem, stream, chain, args...)
 // launches kern; with chain set the launch carries the programmatic stream
@@ -26,9 +27,6 @@
 namespace veckm {
 
 __device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void chain_release() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,

@@ -186,6 +186,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int &total) {
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restrict__ cnt, int64_t P,
                                                               int *__restrict__ bsum) {
   __shared__ int s_warp[33];
+  chain_wait();
   const int64_t b0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
   int v = 0;
 #pragma unroll
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restr
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(int *__restrict__ bsum, int nb,
                                                            int *__restrict__ total_out) {
   __shared__ int s_warp[33];
+  chain_wait();
   int carry = 0;
   for (int base = 0; base < nb; base += kScanThreads) {
     const int i = base + threadIdx.x;
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
                                                              int *__restrict__ off,
                                                              int *__restrict__ cur) {
   __shared__ int s_warp[33];
+  chain_wait();
   const int64_t b0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
   int c[kScanPer];
   int v = 0;
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
 
 __global__ void __launch_bounds__(256) k_place(Events ev, Geometry g, int *__restrict__ cur,
                                                int2 *__restrict__ rec, int *__restrict__ pix) {
+  chain_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < ev.n;
        k0 += stride * kPlaceILP) {
@@ -336,7 +340,6 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geo
                                                                   int *__restrict__ err,
                                                                   float *__restrict__ zero_flow) {
   __shared__ int h[kMaxBuckets];
-  chain_release();  // the scan may launch now
   for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const TileEvents te(ev, per_tile);
@@ -377,7 +380,6 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const int *__restrict__ bh
                                                       int *__restrict__ btot) {
   __shared__ int s_warp[33];
   chain_wait();
-  chain_release();
   const int b = blockIdx.x;
   const int i0 = 4 * threadIdx.x;
   int c[4], v = 0;
@@ -411,7 +413,6 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_scatter(Events ev, G
   __shared__ int fil[kMaxBuckets];  // fill cursor of each run
   __shared__ int s_warp[33];
   chain_wait();
-  chain_release();
   const int *cnt_tile = bhist + (size_t)blockIdx.x * nb;
   block_scan_small(btot, nb, cur, nullptr, s_warp);  // bucket bases
   int nvalid;
@@ -485,7 +486,6 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_bucket_sort(const int4 *__r
   __shared__ int s_warp[33];
   __shared__ int s_base[2];
   chain_wait();
-  chain_release();
   const int b = blockIdx.x;
   const int64_t p0 = (int64_t)b << shift;
   // this bucket's first record: the sum of the earlier buckets' totals
@@ -642,7 +642,6 @@ __global__ void __launch_bounds__(256) k_pixsum(Geometry g, Tables tb, const int
                                                 const int *__restrict__ rpix,
                                                 float4 *__restrict__ acc, int recs) {
   chain_wait();
-  chain_release();
   constexpr int U = 32 * DV;
   const int lane = threadIdx.x & 31;
   const int64_t ns = *nsorted;
@@ -745,7 +744,6 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
                                                  const int *__restrict__ occ = nullptr) {
   static_assert(EMIT == kEmitF32 || P == Pass::Cols, "normalised output: column pass only");
   chain_wait();
-  chain_release();
   constexpr bool HALF = EMIT == kEmitF16N;
   constexpr bool NORM = HALF;  // divided by the window counts
   constexpr int U = 32 * DV;
@@ -1192,6 +1190,7 @@ __global__ void __launch_bounds__(256) k_pixsum_owned(Tables tb, const int *__re
                                                       const int2 *__restrict__ rec,
                                                       const int *__restrict__ rpix,
                                                       float4 *__restrict__ acc) {
+  chain_wait();
   constexpr int U = 32 * DV;
   const int lane = threadIdx.x & 31;
   const int64_t ns = *nsorted;
@@ -1284,6 +1283,7 @@ __global__ void __launch_bounds__(32 * kDirWarps) k_direct(Events ev, const int6
     }
     __syncthreads();
   }
+  chain_wait();  // the prologue above reads only the weights
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int D = 2 * U;
   uint2 w[DV][2];
@@ -1464,18 +1464,20 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
 
 template <int DV>
 int pixsum_owned_impl(const Tables &tb, const int *nsorted, const int2 *rec, const int *rpix,
-                      int64_t n, float4 *acc, cudaStream_t s) {
+                      int64_t n, float4 *acc, cudaStream_t s, bool chain) {
   if (n == 0) return 0;
   const int64_t warps = (n + kPixRecs - 1) / kPixRecs;
   const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 64);
-  k_pixsum_owned<DV><<<grid, 256, 0, s>>>(tb, nsorted, rec, rpix, acc);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_kernel(k_pixsum_owned<DV>, dim3(grid), dim3(256), 0, s, chain, tb, nsorted, rec,
+                       rpix, acc) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 template <int DV, bool FLOW>
 int direct_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                 const Tables &tb, const float4 *acc, const int *cnt, const MLP &mlp, float *out,
-                int *err, cudaStream_t s) {
+                int *err, cudaStream_t s, bool chain) {
   if (nK == 0) return 0;
   constexpr int IN = 128 * DV;
   const size_t sm = sizeof(float) * ((FLOW ? (size_t)IN * kHid : 0) + (size_t)kDirWarps * IN + 3 * kHid);
@@ -1484,8 +1486,10 @@ int direct_impl(const Events &ev, const int64_t *K, int64_t nK, const Geometry &
   const int per_sm = std::max(1, blocks_per_sm((const void *)kern, 32 * kDirWarps, sm));
   const int64_t blocks = (nK + kDirWarps - 1) / kDirWarps;
   const int grid = (int)std::min<int64_t>(blocks, (int64_t)num_sms() * per_sm);
-  kern<<<grid, 32 * kDirWarps, sm, s>>>(ev, K, nK, g, tb, acc, cnt, mlp, out, err);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_kernel(kern, dim3(grid), dim3(32 * kDirWarps), sm, s, chain, ev, K, nK, g, tb, acc,
+                       cnt, mlp, out, err) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 template <int DV>
@@ -1564,22 +1568,29 @@ int launch_hist(const Events &ev, const Geometry &g, int *cnt, int *err, float *
 int scan_blocks(int64_t P) { return (int)((P + kScanBlock - 1) / kScanBlock); }
 
 int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur, int *total,
-                cudaStream_t s) {
+                cudaStream_t s, bool chain) {
   const int64_t P = (int64_t)g.W * g.H;
   const int nb = scan_blocks(P);
-  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(cnt, P, bsum);
-  k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb, total);
-  k_scan_apply<<<nb, kScanThreads, 0, s>>>(cnt, P, bsum, off, cur);
-  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+  // the second and third kernels are chained to the one before them
+  return launch_kernel(k_scan_reduce, dim3(nb), dim3(kScanThreads), 0, s, chain, cnt, P, bsum) ==
+                     cudaSuccess &&
+                 launch_kernel(k_scan_top, dim3(1), dim3(kScanThreads), 0, s, true, bsum, nb,
+                               total) == cudaSuccess &&
+                 launch_kernel(k_scan_apply, dim3(nb), dim3(kScanThreads), 0, s, true, cnt, P,
+                               bsum, off, cur) == cudaSuccess
+             ? 3
+             : -1;
 }
 
 int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool chain) {
   if (ev.n == 0) return 0;
   const int grid = (int)std::min<int64_t>((ev.n + 256 * kPlaceILP - 1) / (256 * kPlaceILP),
                                           (int64_t)num_sms() * 8);
-  k_place<<<grid, 256, 0, s>>>(ev, g, cur, rec, pix);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_kernel(k_place, dim3(grid), dim3(256), 0, s, chain, ev, g, cur, rec, pix) ==
+                 cudaSuccess
+             ? 1
+             : -1;
 }
 
 int bucket_sort_shift(int64_t P) {
@@ -1657,18 +1668,20 @@ int launch_pixsum(const Geometry &g, const Tables &tb, const int *nsorted, const
 }
 
 int launch_pixsum_owned(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                        const int *rpix, int64_t n, float4 *acc, cudaStream_t s) {
-  VECKM_DISPATCH_DV(g.U, (pixsum_owned_impl<DV>(tb, nsorted, rec, rpix, n, acc, s)));
+                        const int *rpix, int64_t n, float4 *acc, cudaStream_t s, bool chain) {
+  VECKM_DISPATCH_DV(g.U, (pixsum_owned_impl<DV>(tb, nsorted, rec, rpix, n, acc, s, chain)));
 }
 
 int launch_direct(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                   const Tables &tb, const float4 *acc, const int *cnt, const MLP *mlp, float *out,
-                  int *err, cudaStream_t s) {
+                  int *err, cudaStream_t s, bool chain) {
   if (mlp) {
     if (g.U > 64) return -2;  // W1 transposed in shared memory: 2D x 128 floats
-    VECKM_DISPATCH_DV(g.U, (direct_impl<DV, true>(ev, K, nK, g, tb, acc, cnt, *mlp, out, err, s)));
+    VECKM_DISPATCH_DV(g.U, (direct_impl<DV, true>(ev, K, nK, g, tb, acc, cnt, *mlp, out, err, s,
+                                                  chain)));
   }
-  VECKM_DISPATCH_DV(g.U, (direct_impl<DV, false>(ev, K, nK, g, tb, acc, cnt, MLP{}, out, err, s)));
+  VECKM_DISPATCH_DV(g.U, (direct_impl<DV, false>(ev, K, nK, g, tb, acc, cnt, MLP{}, out, err, s,
+                                                 chain)));
 }
 
 int launch_pool_rows(const Geometry &g, const Tables &tb, const float4 *acc, float4 *hbuf,

@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <new>
 
+#include "chain.cuh"
 #include "ctx.h"
 #include "check.cuh"
 #include "phase.cuh"
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tmax_reduce(const unsigned *__r
                                                              long long n,
                                                              unsigned *__restrict__ bmax) {
   __shared__ unsigned s_warp[33];
+  chain_wait();
   const long long b0 = (long long)blockIdx.x * kMaxBlock + threadIdx.x * kMaxPer;
   unsigned v = 0;
 #pragma unroll
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tmax_reduce(const unsigned *__r
 
 __global__ void __launch_bounds__(kMaxThreads) k_tmax_top(unsigned *__restrict__ bmax, int nb) {
   __shared__ unsigned s_warp[33];
+  chain_wait();
   unsigned carry = 0;
   for (int base = 0; base < nb; base += kMaxThreads) {
     const int i = base + threadIdx.x;
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tmax_order(const unsigned *__re
                                                             const RingState *st,
                                                             int *__restrict__ flag, int *err) {
   __shared__ unsigned s_warp[33];
+  chain_wait();
   const long long b0 = (long long)blockIdx.x * kMaxBlock + threadIdx.x * kMaxPer;
   unsigned k[kMaxPer];
   unsigned v = 0;
@@ -177,6 +181,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tmax_order(const unsigned *__re
 // t); then how many of the `*nvalid` valid packet events fit the ring
 __global__ void k_ring_tail(RingState *st, const uint32_t *__restrict__ rt, long long cap,
                             uint32_t t_lo, const int *__restrict__ nvalid) {
+  chain_wait();
   const long long n = nvalid ? *nvalid : 0;
   const int lane = threadIdx.x & 31;
   const long long head = st->head, tail0 = st->tail;
@@ -217,6 +222,7 @@ __global__ void __launch_bounds__(256)
                  const uint32_t *__restrict__ rt, long long cap, int W, int U, long long npx,
                  const uint2 *__restrict__ wt, long long *__restrict__ acc64,
                  int *__restrict__ cnt, uint8_t *__restrict__ dirty) {
+  chain_wait();
   const int lane = threadIdx.x & 31;
   const long long first = sign < 0 ? st->tail_old : st->head_old;
   const long long count = sign < 0 ? st->tail - st->tail_old : st->app;
@@ -261,6 +267,7 @@ __global__ void k_ring_append(const RingState *st, const int16_t *__restrict__ x
                               const int *__restrict__ off, int16_t *__restrict__ rx,
                               int16_t *__restrict__ ry, uint32_t *__restrict__ rt, long long cap,
                               int64_t *__restrict__ K, int *err) {
+  chain_wait();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (!flag[i]) {
@@ -282,6 +289,7 @@ __global__ void k_ring_append(const RingState *st, const int16_t *__restrict__ x
 // the ring's times ascend, so the last appended event holds the largest
 // accepted time
 __global__ void k_ring_advance(RingState *st, const uint32_t *__restrict__ rt, long long cap) {
+  chain_wait();
   if (threadIdx.x != 0) return;
   st->head = st->head_old + st->app;
   if (st->app > 0) st->t_last = rt[(st->head - 1) % cap];
@@ -296,6 +304,7 @@ __global__ void __launch_bounds__(256) k_fixed_to_float_dirty(const long long *_
                                                               float4 *__restrict__ acc,
                                                               uint8_t *__restrict__ dirty,
                                                               long long P, int U) {
+  chain_wait();
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   const float s = 2.3283064365386963e-10f;  // 2^-32
@@ -408,42 +417,56 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   grids_dirty(c);  // the push pools through hbuf into acc
   const uint32_t t_lo = t_hi_us >= (uint64_t)s->window ? t_hi_us - (uint32_t)s->window : 0u;
   const int DV = g.U / 32;
+  // Every kernel of a push after the first is chained to the one before it
+  // (programmatic dependent launch, chain.cuh), except the column pass, which
+  // follows the join with the side stream.  Launch errors are read back below
+  // (cudaPeekAtLastError).
   auto apply = [&](int sign) {
-    const int blocks = num_sms() * 8;
+    const dim3 blocks(num_sms() * 8);
+    const long long npx = (long long)g.W * g.H;
+#define VECKM_APPLY(DV_)                                                                     \
+  (void)launch_kernel(k_ring_apply<DV_>, blocks, dim3(256), 0, cs, true, s->st, sign, s->rx,    \
+                      s->ry, s->rt, s->cap, g.W, g.U, npx, c->wt, s->acc64, s->cnt, s->dirty)
     switch (DV) {
-      case 1: k_ring_apply<1><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
-      case 2: k_ring_apply<2><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
-      case 3: k_ring_apply<3><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
-      default: k_ring_apply<4><<<blocks, 256, 0, cs>>>(s->st, sign, s->rx, s->ry, s->rt, s->cap, g.W, g.U, (long long)g.W * g.H, c->wt, s->acc64, s->cnt, s->dirty); break;
+      case 1: VECKM_APPLY(1); break;
+      case 2: VECKM_APPLY(2); break;
+      case 3: VECKM_APPLY(3); break;
+      default: VECKM_APPLY(4); break;
     }
+#undef VECKM_APPLY
   };
   int launches = 0;
   // 1. valid events and their places
   if (n > 0) {
     k_ring_flags<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(d_x, d_y, d_t, n, g.W, g.H, t_lo, t_hi_us, s->flag, s->tkey, c->err);
     const int nbm = (int)((n + kMaxBlock - 1) / kMaxBlock);
-    k_tmax_reduce<<<nbm, kMaxThreads, 0, cs>>>(s->tkey, n, s->bmax);
-    k_tmax_top<<<1, kMaxThreads, 0, cs>>>(s->bmax, nbm);
-    k_tmax_order<<<nbm, kMaxThreads, 0, cs>>>(s->tkey, n, s->bmax, s->st, s->flag, c->err);
+    (void)launch_kernel(k_tmax_reduce, dim3(nbm), dim3(kMaxThreads), 0, cs, true, s->tkey, n,
+                        s->bmax);
+    (void)launch_kernel(k_tmax_top, dim3(1), dim3(kMaxThreads), 0, cs, true, s->bmax, nbm);
+    (void)launch_kernel(k_tmax_order, dim3(nbm), dim3(kMaxThreads), 0, cs, true, s->tkey, n,
+                        s->bmax, s->st, s->flag, c->err);
     launches += 3;
     Geometry line{};
     line.W = (int)n;
     line.H = 1;
-    const int r = launch_scan(line, s->flag, s->bsum, s->off, s->cur, s->nvalid, cs);
+    const int r = launch_scan(line, s->flag, s->bsum, s->off, s->cur, s->nvalid, cs, true);
     if (r < 0) return fail_cuda(cudaGetLastError(), "stream scan launch");
     launches += 1 + r;
   }
-  // 2-3. expire
-  k_ring_tail<<<1, 32, 0, cs>>>(s->st, s->rt, s->cap, t_lo, n > 0 ? s->nvalid : nullptr);
+  // 2-3. expire (the first kernel of a push without events keeps full order)
+  (void)launch_kernel(k_ring_tail, dim3(1), dim3(32), 0, cs, n > 0, s->st, s->rt, s->cap, t_lo,
+                      n > 0 ? s->nvalid : nullptr);
   apply(-1);
   launches += 2;
   // 4-5. append and add
   if (n > 0) {
-    k_ring_append<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(s->st, d_x, d_y, d_t, n, s->flag, s->off, s->rx, s->ry, s->rt, s->cap, s->K, c->err);
+    (void)launch_kernel(k_ring_append, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, cs, true,
+                        s->st, d_x, d_y, d_t, n, s->flag, s->off, s->rx, s->ry, s->rt, s->cap,
+                        s->K, c->err);
     apply(+1);
     launches += 2;
   }
-  k_ring_advance<<<1, 32, 0, cs>>>(s->st, s->rt, s->cap);
+  (void)launch_kernel(k_ring_advance, dim3(1), dim3(32), 0, cs, true, s->st, s->rt, s->cap);
   launches += 1;
   cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) {
@@ -477,12 +500,14 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
     launches += r;
   }
   const long long P = (long long)g.W * g.H;
-  k_fixed_to_float_dirty<<<(unsigned)std::min<long long>((P + 255) / 256, (long long)num_sms() * 8),
-                           256, 0, cs>>>(s->acc64, s->accf, s->dirty, P, g.U);
+  if (launch_kernel(k_fixed_to_float_dirty,
+                    dim3((unsigned)std::min<long long>((P + 255) / 256, (long long)num_sms() * 8)),
+                    dim3(256), 0, cs, true, s->acc64, s->accf, s->dirty, P, g.U) != cudaSuccess)
+    return fail_cuda(cudaGetLastError(), "stream conversion launch");
   launches += 1;
   const Tables tb = c->tables();
   const Tune tn = c->tune_for(g);
-  if ((r = launch_pool_rows(g, tb, s->accf, c->hbuf, cs, tn)) < 0) return fail_cuda(cudaGetLastError(), "pooling (rows) launch");
+  if ((r = launch_pool_rows(g, tb, s->accf, c->hbuf, cs, tn, nullptr, true)) < 0) return fail_cuda(cudaGetLastError(), "pooling (rows) launch");
   launches += r;
   if (join.armed) {
     cudaStreamWaitEvent(cs, c->ev_join, 0);
@@ -502,7 +527,7 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
     MLP m = c->mlp();
     m.pooled_half = half_grid ? 1 : 0;
     r = launch_predict_tc(ev, s->K, n, nullptr, nullptr, nullptr, g, tb, c->acc, c->ncnt, m,
-                          d_out, c->err, cs, tn);
+                          d_out, c->err, cs, tn, nullptr, 0, nullptr, true);
   } else {
     r = launch_predict_fp32(ev, s->K, n, nullptr, nullptr, nullptr, g, tb, c->acc, c->ncnt,
                             c->mlp(), d_out, c->err, cs);

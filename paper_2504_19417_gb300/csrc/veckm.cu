@@ -327,21 +327,32 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
   // Both give the per-pixel counts, the record total (off[P]) and the
   // pixel-grouped records.
   float *zero_flow = (sorted && !direct) ? out : nullptr;
+  // A launch that follows a kernel of this step in s (after_kernel) is
+  // chained to it (programmatic dependent launch, chain.cuh); the step's
+  // first kernel and the first after a memset or a join with the side stream
+  // keep full ordering.  Event records in between (the forks) change nothing.
+  // The stage timing's marks (event records) sit between stages: with timing
+  // on, the launches after a mark are plain (chain_marked), so that each
+  // stage's events bracket its own kernels in full order.
+  bool after_kernel = false;
+  const bool chain_marked = !c->timing;
   if (bucketed) {
     if ((r = launch_bucket_sort(ev, g, c->cnt, c->off + P, c->rec, c->rpix, c->brec, c->bhist,
                                 c->btot, c->err, zero_flow, s,
                                 sparse_rows && !direct ? gsum : nullptr)) < 0)
       return cuda_fail(cudaGetLastError(), "bucket sort launch");
     launches += r;
+    after_kernel = r > 0;
   } else {
     cudaError_t e = cudaMemsetAsync(c->cnt, 0, P * sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the counts");
     if ((r = launch_hist(ev, g, c->cnt, c->err, zero_flow, s)) < 0)
       return cuda_fail(cudaGetLastError(), "histogram launch");
     launches += r;
-    if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s)) < 0)
+    if ((r = launch_scan(g, c->cnt, c->bsum, c->off, c->cur, c->total, s, r > 0)) < 0)
       return cuda_fail(cudaGetLastError(), "scan launch");
     launches += r;
+    after_kernel = true;
   }
   // The window counts need only the per-pixel counts: on the dense path they
   // run on the side stream, under the pixel sums and row pass, and join
@@ -357,23 +368,25 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     launches += r;
   }
   if (!bucketed) {
-    if ((r = launch_place(ev, g, c->cur, c->rec, c->rpix, s)) < 0)
+    if ((r = launch_place(ev, g, c->cur, c->rec, c->rpix, s, true)) < 0)
       return cuda_fail(cudaGetLastError(), "placement launch");
     launches += r;
   }
   mark();
   if (direct) {
     if (c->zero_grid == 0) c->zero_grid = -1;  // the owned sums write acc
-    if ((r = launch_pixsum_owned(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s)) < 0)
+    if ((r = launch_pixsum_owned(g, tb, c->off + P, c->rec, c->rpix, n, c->acc, s,
+                                 after_kernel && chain_marked)) < 0)
       return cuda_fail(cudaGetLastError(), "pixel sum launch");
     launches += r;
+    after_kernel = after_kernel || r > 0;
     mark();
     mark();  // no row pass, window counts or column pass
     mark();
     mark();
     MLP m = c->mlp();
     if ((r = launch_direct(ev, K, nK, g, tb, c->acc, c->cnt, what == Out::Flow ? &m : nullptr,
-                           out, c->err, s)) < 0)
+                           out, c->err, s, after_kernel && chain_marked)) < 0)
       return cuda_fail(cudaGetLastError(), "direct window launch");
     launches += r;
     mark();
@@ -381,17 +394,15 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     c->last_launches = launches;
     return VECKM_OK;
   }
-  // Launches that follow a kernel of this step in s, with no event wait
-  // between them, are chained to it (programmatic dependent launch): the
-  // pixel sums to the bucket sort, the row pass to the pixel sums, the head
-  // to the column pass.  The column pass follows the join with the side
-  // stream and is launched in full order.
-  const bool chain_sums = bucketed && !zjoin.armed;
+  // The pixel sums are chained to the sort unless they wait for the clear,
+  // the row pass to the pixel sums, the head to the column pass; the column
+  // pass follows the join with the side stream.
+  const bool chain_sums = after_kernel && !zjoin.armed && chain_marked;
   zjoin.wait();  // the clear of gsum (side stream)
   if ((r = launch_pixsum(g, tb, c->off + P, c->rec, c->rpix, n, gsum, s, false, chain_sums)) < 0)
     return cuda_fail(cudaGetLastError(), "pixel sum launch");
   launches += r;
-  const bool chain_rows = r > 0;
+  const bool chain_rows = r > 0 && chain_marked;
   mark();
   if ((r = launch_pool_rows(g, tb, gsum, grow, s, tn, sparse_rows ? c->cnt : nullptr,
                             chain_rows)) < 0)
@@ -423,7 +434,8 @@ veckm_status run_pipeline(veckm_ctx *c, const Geometry &g, const Events &ev, con
     // a cleared grid serves only a next call whose sums cannot do without one
     r = launch_predict_tc(ev, K, nK, sorted ? c->rec : nullptr, sorted ? c->rpix : nullptr,
                           c->off + P, g, tb, gsum, c->ncnt, m, out, c->err, s, tn,
-                          may_zero && !sparse_rows ? grow : nullptr, units, &zeroed, true);
+                          may_zero && !sparse_rows ? grow : nullptr, units, &zeroed,
+                          chain_marked);
     if (r >= 0 && zeroed && !capturing) {
       c->zero_grid = grow == c->acc ? 0 : 1;
       c->zero_units = units;

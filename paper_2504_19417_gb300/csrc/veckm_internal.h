@@ -93,9 +93,9 @@ int launch_hist(const Events &ev, const Geometry &g, int *cnt, int *err, float *
                 cudaStream_t s);
 int scan_blocks(int64_t P);
 int launch_scan(const Geometry &g, const int *cnt, int *bsum, int *off, int *cur, int *total,
-                cudaStream_t s);
+                cudaStream_t s, bool chain = false);
 int launch_place(const Events &ev, const Geometry &g, int *cur, int2 *rec, int *pix,
-                 cudaStream_t s);
+                 cudaStream_t s, bool chain = false);
 // The same outputs as launch_hist + launch_scan + launch_place (counts per
 // pixel, the record total in *total, pixel-grouped records) by a two-level
 // bucket sort without global atomics.  bucket_sort_shift: log2 of the pixels
@@ -177,10 +177,11 @@ void grids_dirty(veckm_ctx *c);
 // clear), then one warp per requested event summing its window (mlp == NULL:
 // the encoding to out [nK][2D]; else the flows to out [nK][2], D <= 128).
 int launch_pixsum_owned(const Geometry &g, const Tables &tb, const int *nsorted, const int2 *rec,
-                        const int *rpix, int64_t n, float4 *acc, cudaStream_t s);
+                        const int *rpix, int64_t n, float4 *acc, cudaStream_t s,
+                        bool chain = false);
 int launch_direct(const Events &ev, const int64_t *K, int64_t nK, const Geometry &g,
                   const Tables &tb, const float4 *acc, const int *cnt, const MLP *mlp, float *out,
-                  int *err, cudaStream_t s);
+                  int *err, cudaStream_t s, bool chain = false);
 
 int num_sms();
 
