@@ -383,12 +383,19 @@ def run_ours(args):
     clocks = ClockSampler(local)
     if not args.lean:
         clocks.start()
-    enc.set_timing(not args.lean)
     total_ms, per, wall = timed(args.steps)
     launches_per_step = enc.last_launch_count()
-    stage_ms, stage_calls = enc.stage_times() if not args.lean else ({}, {})
-    enc.set_timing(False)
     clk = clocks.stop() if not args.lean else None
+    # Stage times: a second timed pass of the same steps with the library's
+    # per-stage event marks on.  With the marks on, the library launches each
+    # stage after a mark in full order instead of chained to the kernel before
+    # it, so the step above is timed without them.
+    stage_ms, stage_calls = {}, {}
+    if not args.lean:
+        enc.set_timing(True)
+        timed(args.steps)
+        stage_ms, stage_calls = enc.stage_times()
+        enc.set_timing(False)
     enc.sync_status()
     value = job_rate(ws, nK, args.steps, total_ms)
     out = {
@@ -440,6 +447,8 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": kd["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
+    roof["timing"] = ("CUDA events on the launching stream around each stage, a second timed "
+                      "pass of the same steps with the stage marks on")
     roof["peak_source"] = pk["source"]
     tr = _kernel_traffic(dom, args.workload)
     roof["traffic"] = tr
@@ -641,7 +650,8 @@ def stream_leg(args, mode, stream):
 def small_leg(args, mode, stream):
     """The small single-slice case: 346x260, 20,000 events over 10 ms (D = 64,
     21x21 window), every event requested; the chosen mode and the plain FP32
-    form, per call with the inputs resident (p50 and p99 over the timed calls),
+    form, per call with the inputs resident (the mean over back-to-back calls;
+    p50 and p99 from a second pass with an event after each call),
     the chosen mode also as a one-slice captured plan, and the flows' error
     against the FP64 oracle on every event."""
     import torch
@@ -670,6 +680,17 @@ def small_leg(args, mode, stream):
         for _ in range(args.warmup):
             enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
         k = max(10, args.steps)
+        # the mean over back-to-back calls (two events around all of them),
+        # then p50/p99 from an event after each call
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for i in range(k):
+            enc.predict(x, y, t, sl.t_ref, out=flow, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        mean_ms = a.elapsed_time(b) / k
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         torch.cuda.synchronize()
         evs[0].record(stream)
@@ -680,8 +701,8 @@ def small_leg(args, mode, stream):
         per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(k)])
         f = flow.cpu().numpy().astype(np.float64)
         rel = np.linalg.norm(f - fref, axis=1) / np.maximum(nref, floor)
-        res[name] = {"flows_per_s": sl.n / (float(per.mean()) * 1e-3),
-                     "ms_per_call": float(per.mean()), "p50_ms": float(np.percentile(per, 50)),
+        res[name] = {"flows_per_s": sl.n / (mean_ms * 1e-3),
+                     "ms_per_call": mean_ms, "p50_ms": float(np.percentile(per, 50)),
                      "p99_ms": float(np.percentile(per, 99)),
                      "kernels_per_call": enc.last_launch_count(),
                      "flow_rel_max": float(rel.max()), "flow_rel_mean": float(rel.mean()),
@@ -693,6 +714,15 @@ def small_leg(args, mode, stream):
     for _ in range(args.warmup):
         plan.launch(stream)
     k = max(10, args.steps)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for i in range(k):
+        plan.launch(stream)
+    b.record(stream)
+    b.synchronize()
+    mean_ms = a.elapsed_time(b) / k
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
     torch.cuda.synchronize()
     evs[0].record(stream)
@@ -703,8 +733,8 @@ def small_leg(args, mode, stream):
     per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(k)])
     f = flow.cpu().numpy().astype(np.float64)
     rel = np.linalg.norm(f - fref, axis=1) / np.maximum(nref, floor)
-    res[args.mode + "_plan"] = {"flows_per_s": sl.n / (float(per.mean()) * 1e-3),
-                                "ms_per_call": float(per.mean()),
+    res[args.mode + "_plan"] = {"flows_per_s": sl.n / (mean_ms * 1e-3),
+                                "ms_per_call": mean_ms,
                                 "p50_ms": float(np.percentile(per, 50)),
                                 "p99_ms": float(np.percentile(per, 99)),
                                 "kernels_per_call": plan.kernel_count,
@@ -744,16 +774,20 @@ def sparse_leg(args, mode, stream):
         enc.set_path(path)
         for _ in range(args.warmup):
             enc.predict(x, y, t, sl.t_ref, K=K, out=flow, stream=stream)
-        enc.set_timing(True)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
         k = max(3, args.steps // 2)
-        a.record(stream)
-        for _ in range(k):
-            enc.predict(x, y, t, sl.t_ref, K=K, out=flow, stream=stream)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b) / k
+        # the calls timed without the stage marks, then again with them for
+        # the stage times (with the marks on, stages launch in full order)
+        for timing in (False, True):
+            enc.set_timing(timing)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                enc.predict(x, y, t, sl.t_ref, K=K, out=flow, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if not timing:
+                ms = a.elapsed_time(b) / k
         st, calls = enc.stage_times()
         enc.set_timing(False)
         stages[name] = {s_: 1000 * v / max(1, calls[s_]) for s_, v in st.items()}
