@@ -284,17 +284,34 @@ def test_host_entry_point_matches_device_entry_point():
         _check_flow(host_k, emb_ref[K], w, mode)
 
 
-def test_stage_timing_records_every_call():
+@pytest.mark.parametrize("mode", [vk.MLP_FP32, vk.MLP_FP16])
+def test_stage_timing_records_every_call(mode):
+    # With stage timing on, the stages after each timing mark launch in full
+    # order instead of chained to the kernel before them: both launch forms
+    # give the oracle's flows, in the dense and the direct window form.
     sl = synth.event_slice(100, 80, 4_000, 10_000, seed=2)
-    enc, _, _ = make(sl, 64)
+    enc, TXY, w = make(sl, 64, mode=mode)
+    emb_ref = _oracle_emb(sl, 64, 10, 10, 16_000, TXY)
     x, y, t = to_dev(sl)
-    enc.set_timing(True)
-    for _ in range(3):
-        enc.predict(x, y, t, sl.t_ref)
-    ms, calls = enc.stage_times()
-    assert all(v == 3 for v in calls.values())
-    assert all(v >= 0 for v in ms.values()) and ms["pool_rows"] > 0
-    assert enc.last_launch_count() >= 4
+    for path in (vk.PATH_DENSE, vk.PATH_DIRECT):
+        enc.set_path(path)
+        chained = enc.predict(x, y, t, sl.t_ref).cpu().numpy()
+        enc.set_timing(True)
+        for _ in range(3):
+            timed = enc.predict(x, y, t, sl.t_ref)
+        ms, calls = enc.stage_times()
+        enc.set_timing(False)
+        assert all(v == 3 for v in calls.values())
+        assert all(v >= 0 for v in ms.values())
+        assert ms["pool_rows" if path == vk.PATH_DENSE else "gather"] > 0
+        assert enc.last_launch_count() >= 4
+        if mode == vk.MLP_FP32 or path == vk.PATH_DENSE:  # the direct form's head is FP32
+            _check_flow(chained, emb_ref, w, mode)
+            _check_flow(timed.cpu().numpy(), emb_ref, w, mode)
+        else:
+            _check_flow(chained, emb_ref, w, vk.MLP_FP32)
+            _check_flow(timed.cpu().numpy(), emb_ref, w, vk.MLP_FP32)
+    enc.sync_status()
 
 
 @pytest.mark.parametrize("mode", [vk.MLP_FP16, vk.MLP_BF16, vk.MLP_FP32, vk.MLP_FP16 | vk.ACC_FP16])
