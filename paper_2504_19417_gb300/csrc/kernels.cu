@@ -736,7 +736,10 @@ enum class Pass { Rows, Cols };
 // none are taken as zero without reading src, whose rows there may hold
 // anything.
 enum : int { kEmitF32 = 0, kEmitF16N = 1, kEmitF32P = 2 };
-template <int DV, Pass P, int EMIT = kEmitF32>
+// LC: the window length 2r + 1 fixed at compile time (the launcher picks the
+// instantiation that matches), so that the per-block loops unroll and their
+// shared-memory loads issue ahead of the dependent sums; 0: any length.
+template <int DV, Pass P, int EMIT = kEmitF32, int LC = 0>
 __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
                                                  int seg, int nseg, int up,
@@ -749,7 +752,8 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   constexpr int U = 32 * DV;
   extern __shared__ float4 smem[];
   const int r = (P == Pass::Rows) ? g.dx : g.dy;
-  const int L = 2 * r + 1;
+  const int L = LC > 0 ? LC : 2 * r + 1;
+  constexpr int kUnroll = LC > 0 ? LC : 1;
   const int SL = (L + 1) * U;  // slot: L data rows + 1 anchor row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -806,6 +810,7 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
         on = __ballot_sync(kFull, occ_v != 0);
         load_occ(b + 1);
       }
+#pragma unroll kUnroll
       for (int q = 0; q < L; ++q) {
         const int pos = in0 + b * L + q;
         const bool rd = pos >= 0 && pos < len && ((on >> (q & 31)) & 1u);
@@ -835,6 +840,7 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     float4 run[DV];
 #pragma unroll
     for (int v = 0; v < DV; ++v) run[v] = f4zero();
+#pragma unroll kUnroll
     for (int q = L - 1; q >= 0; --q) {
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
@@ -860,6 +866,7 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     float4 ph[DV];
 #pragma unroll
     for (int v = 0; v < DV; ++v) ph[v] = cmul2(sl[L * U + lane + 32 * v], fl[v]);
+#pragma unroll kUnroll
     for (int q = 0; q < L; ++q) {
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
@@ -939,7 +946,9 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
 #pragma unroll
     for (int v = 0; v < DV; ++v) G[v] = f4zero();
     const int qmax = min(L - 1, nout - 1 - j0);
-    for (int q = 0; q < qmax; ++q) {
+#pragma unroll kUnroll
+    for (int q = 0; q < L - 1; ++q) {
+      if (q >= qmax) break;
 #pragma unroll
       for (int v = 0; v < DV; ++v) G[v] = add4(G[v], V[q * U + lane + 32 * v]);
       emit(j0 + q + 1, q + 1, G);  // suffix of block b from q+1, prefix of block b+1 to q
@@ -1453,10 +1462,12 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
   if (wpb_req > 0 && wpb_req <= 4 && per_warp * wpb_req <= kBoxSmemMax) wpb = wpb_req;
   const size_t sm = per_warp * wpb;
-  if (set_smem(k_box_pass<1, P, EMIT>, sm) != cudaSuccess) return -1;
+  // the default window (radius 10) has an instantiation with its length fixed
+  auto kern = L == 21 ? k_box_pass<1, P, EMIT, 21> : k_box_pass<1, P, EMIT, 0>;
+  if (set_smem(kern, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const dim3 grid((unsigned)((warps + wpb - 1) / wpb), DV);
-  return launch_kernel(k_box_pass<1, P, EMIT>, grid, dim3(32 * wpb), sm, s, chain, src, dst, g, tb,
+  return launch_kernel(kern, grid, dim3(32 * wpb), sm, s, chain, src, dst, g, tb,
                        seg, nseg, 32 * DV, ncnt, occ) == cudaSuccess
              ? 1
              : -1;
