@@ -32,9 +32,12 @@
 // exp(i x X/dx) = tx[x] and exp(i y Y/dy) = ty[y]; the temporal phase
 // exp(i t T/dt) comes from exact fixed-point argument reduction (phase.cuh),
 // so no trigonometric function ever sees an argument outside [-pi, pi).
-// Inside a box-pass block the spatial phase advances by the exact step rows
-// exp(i X/dx), exp(i Y/dy) from a table anchor (at most 2*radius+1 steps, so
-// the recurrence adds at most ~(2r+1) x 1.2e-7 relative error).
+// Inside a box-pass block the spatial phase advances from a table anchor by
+// the exact step rows exp(i X/dx), exp(i Y/dy): in the column pass one step
+// per output (at most 2*radius+1 steps, ~(2r+1) x 1.2e-7 relative error); in
+// the row pass even and odd positions as two rotations by the squared step
+// (at most radius+1 steps each, ~(r+1) x 2.4e-7 with the squared step's own
+// rounding).
 //
 // Box sums use the van Herk / Gil-Werman block scheme (blocks of the window
 // length L; each window is the suffix of one block plus the prefix of the
@@ -738,7 +741,10 @@ enum class Pass { Rows, Cols };
 enum : int { kEmitF32 = 0, kEmitF16N = 1, kEmitF32P = 2 };
 // LC: the window length 2r + 1 fixed at compile time (the launcher picks the
 // instantiation that matches), so that the per-block loops unroll and their
-// shared-memory loads issue ahead of the dependent sums; 0: any length.
+// shared-memory loads issue ahead of the dependent sums; 0: any length.  With
+// the length fixed, the suffix sums of the block being emitted are held in
+// registers, so a warp's ring needs two slots instead of three (more warps
+// fit on an SM).
 template <int DV, Pass P, int EMIT = kEmitF32, int LC = 0>
 __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src,
                                                  float4 *__restrict__ dst, Geometry g, Tables tb,
@@ -760,7 +766,9 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   const int nlines = (P == Pass::Rows) ? g.H : g.W;
   const int len = (P == Pass::Rows) ? g.W : g.H;
   if (wid >= (int64_t)nlines * nseg) return;
-  float4 *ring = smem + (size_t)warp * 3 * SL;
+  constexpr bool kRegS = LC > 0;         // suffix sums in registers
+  constexpr int kSlots = kRegS ? 2 : 3;  // ring slots per warp
+  float4 *ring = smem + (size_t)warp * kSlots * SL;
   // neighbouring warps take neighbouring lines of the same segment, so the
   // blocks in flight at one time sit side by side in memory
   const int line = (int)(wid % nlines), s = (int)(wid / nlines);
@@ -791,7 +799,7 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   const size_t stride = (P == Pass::Rows) ? (size_t)up : (size_t)g.W * up;
   const int nb = (nout + L - 1) / L;  // output blocks; input blocks 0..nb
 
-  auto slot = [&](int b) { return ring + (size_t)(b % 3) * SL; };
+  auto slot = [&](int b) { return ring + (size_t)(b % kSlots) * SL; };
   // row pass with occ: lane q holds the count of pixel q of the next block to
   // issue, loaded one block ahead of its use
   const bool use_occ = P == Pass::Rows && occ != nullptr && L <= 32;
@@ -836,6 +844,20 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     }
     cp_async_commit();
   };
+  // kRegS: suffix sums of the block being emitted, and its anchor row
+  float4 Sreg[kRegS ? LC : 1][DV], Areg[DV];
+  auto suffix_regs = [&](const float4 *sl) {
+#pragma unroll
+    for (int v = 0; v < DV; ++v) {
+      float4 run = f4zero();
+#pragma unroll
+      for (int q = (kRegS ? LC : 1) - 1; q >= 0; --q) {
+        run = add4(run, sl[q * U + lane + 32 * v]);
+        Sreg[q][v] = run;
+      }
+      Areg[v] = sl[L * U + lane + 32 * v];
+    }
+  };
   auto suffix = [&](float4 *sl) {
     float4 run[DV];
 #pragma unroll
@@ -849,8 +871,8 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
       }
     }
   };
-  // fixed factor of this line and the per-step rotation
-  float4 fl[DV], st[DV];
+  // fixed factor of this line, the per-step rotation and its square (row pass)
+  float4 fl[DV], st[DV], st2[DV];
 #pragma unroll
   for (int v = 0; v < DV; ++v) {
     const int u = lane + 32 * v;
@@ -861,18 +883,28 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
       fl[v] = __ldg(tb.tx + (size_t)(line + g.dx) * up + u0 + u);
       st[v] = __ldg(tb.sy + u0 + u);
     }
+    st2[v] = cmul2(st[v], st[v]);
   }
   auto modulate = [&](float4 *sl) {  // row pass: sl[q] *= tx[x0 + q] ty[y]
-    float4 ph[DV];
+    // the even and odd inputs' phases as two rotations by the squared step:
+    // half as many dependent steps in each
+    float4 pe[DV], po[DV];
 #pragma unroll
-    for (int v = 0; v < DV; ++v) ph[v] = cmul2(sl[L * U + lane + 32 * v], fl[v]);
+    for (int v = 0; v < DV; ++v) {
+      pe[v] = cmul2(sl[L * U + lane + 32 * v], fl[v]);
+      po[v] = cmul2(pe[v], st[v]);
+    }
 #pragma unroll kUnroll
-    for (int q = 0; q < L; ++q) {
+    for (int q = 0; q < L; q += 2) {
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
         float4 *e = sl + q * U + lane + 32 * v;
-        *e = cmul2(*e, ph[v]);
-        ph[v] = cmul2(ph[v], st[v]);
+        *e = cmul2(*e, pe[v]);
+        pe[v] = cmul2(pe[v], st2[v]);
+        if (q + 1 < L) {
+          e[U] = cmul2(e[U], po[v]);
+          po[v] = cmul2(po[v], st2[v]);
+        }
       }
     }
   };
@@ -886,22 +918,32 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
   };
   int cnt_next = NORM ? load_cnt(0) : 0;
 
+  // Blocks stream through the ring one group ahead: with the suffix sums in
+  // registers, block b + 3 goes into the slot of block b + 1 once that
+  // block's suffix sums are taken; otherwise block b + 2 goes into the slot
+  // block b - 1 used, at the start of iteration b.
   issue(0);
   issue(1);
   cp_async_wait1();
   if (P == Pass::Rows) modulate(slot(0));
-  suffix(slot(0));
+  if constexpr (kRegS) {
+    suffix_regs(slot(0));
+    issue(2);
+  } else {
+    suffix(slot(0));
+  }
   for (int b = 0; b < nb; ++b) {
-    issue(b + 2);
+    if constexpr (!kRegS) issue(b + 2);
     cp_async_wait1();  // block b+1 has landed
-    const float4 *S = slot(b);
+    const float4 *S = slot(b);  // (without kRegS) block b's suffix sums
     float4 *V = slot(b + 1);
     if (P == Pass::Rows && b + 1 <= nb) modulate(V);
     const int j0 = b * L;
     float4 dph[DV];  // column pass: phase of the next output, conj applied at emit
     if (P == Pass::Cols) {
 #pragma unroll
-      for (int v = 0; v < DV; ++v) dph[v] = cmul2(fl[v], S[L * U + lane + 32 * v]);
+      for (int v = 0; v < DV; ++v)
+        dph[v] = cmul2(fl[v], kRegS ? Areg[v] : S[L * U + lane + 32 * v]);
     }
     float inv_lane = 0.f;  // NORM: 1/n of output j0 + lane (lanes < L), loaded a block ahead
     if (NORM) {
@@ -922,7 +964,11 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
 #pragma unroll
       for (int v = 0; v < DV; ++v) {
         const int u = lane + 32 * v;
-        float4 o = S[qs * U + u];
+        float4 o;
+        if constexpr (kRegS)
+          o = Sreg[qs][v];
+        else
+          o = S[qs * U + u];
         if (G) o = add4(o, G[v]);
         if (P == Pass::Cols) {
           o = cmul2c(o, dph[v]);
@@ -948,12 +994,18 @@ __global__ void __launch_bounds__(128) k_box_pass(const float4 *__restrict__ src
     const int qmax = min(L - 1, nout - 1 - j0);
 #pragma unroll kUnroll
     for (int q = 0; q < L - 1; ++q) {
-      if (q >= qmax) break;
+      if (q < qmax) {
 #pragma unroll
-      for (int v = 0; v < DV; ++v) G[v] = add4(G[v], V[q * U + lane + 32 * v]);
-      emit(j0 + q + 1, q + 1, G);  // suffix of block b from q+1, prefix of block b+1 to q
+        for (int v = 0; v < DV; ++v) G[v] = add4(G[v], V[q * U + lane + 32 * v]);
+        emit(j0 + q + 1, q + 1, G);  // suffix of block b from q+1, prefix of block b+1 to q
+      }
     }
-    if (b + 1 < nb) suffix(V);
+    if constexpr (kRegS) {
+      if (b + 1 < nb) suffix_regs(V);
+      issue(b + 3);  // into block b+1's slot, now read
+    } else {
+      if (b + 1 < nb) suffix(V);
+    }
   }
   cp_async_wait0();
 }
@@ -1458,12 +1510,17 @@ int box_pass(const Geometry &g, const Tables &tb, const float4 *src, float4 *dst
   const int nseg = (len + seg - 1) / seg;
   // one warp per (line segment, 32-unit slice of the pixels): DV slices, so
   // the ring of a warp holds 32 units per row whatever D is
-  const size_t per_warp = (size_t)3 * (L + 1) * 32 * sizeof(float4);
+  // ring slots per warp: two where the window length has its own
+  // instantiation (suffix sums in registers), else three
+  const bool fixed_len = L == 21 || L == 17;
+  const size_t per_warp = (size_t)(fixed_len ? 2 : 3) * (L + 1) * 32 * sizeof(float4);
   int wpb = per_warp * 2 <= 100 * 1024 ? 2 : 1;
   if (wpb_req > 0 && wpb_req <= 4 && per_warp * wpb_req <= kBoxSmemMax) wpb = wpb_req;
   const size_t sm = per_warp * wpb;
-  // the default window (radius 10) has an instantiation with its length fixed
-  auto kern = L == 21 ? k_box_pass<1, P, EMIT, 21> : k_box_pass<1, P, EMIT, 0>;
+  // the windows of radius 10 and 8 have instantiations with their length fixed
+  auto kern = L == 21   ? k_box_pass<1, P, EMIT, 21>
+              : L == 17 ? k_box_pass<1, P, EMIT, 17>
+                        : k_box_pass<1, P, EMIT, 0>;
   if (set_smem(kern, sm) != cudaSuccess) return -1;
   const int64_t warps = (int64_t)nlines * nseg;
   const dim3 grid((unsigned)((warps + wpb - 1) / wpb), DV);
