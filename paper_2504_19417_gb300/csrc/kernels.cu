@@ -337,7 +337,7 @@ struct TileEvents {
 };
 
 // bhist is tile-major: bhist[tile * nb + bucket]
-__global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geometry g, int shift,
+__global__ void __launch_bounds__(kSortThreads, 3) k_bucket_count(Events ev, Geometry g, int shift,
                                                                   int nb, int per_tile,
                                                                   int *__restrict__ bhist,
                                                                   int *__restrict__ err,
@@ -346,19 +346,22 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_bucket_count(Events ev, Geo
   for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const TileEvents te(ev, per_tile);
-  // kSortILP events per thread and round: every load first, then the atomics
-  for (int jb = threadIdx.x; jb < te.m; jb += kSortILP * blockDim.x) {
-    int x[kSortILP], y[kSortILP];
-    uint32_t t[kSortILP];
+  // kILP events per thread and round: every load first, then the atomics
+  // (fewer than the other sort kernels take, so that three blocks fit an SM
+  // without spills)
+  constexpr int kILP = 6;
+  for (int jb = threadIdx.x; jb < te.m; jb += kILP * blockDim.x) {
+    int x[kILP], y[kILP];
+    uint32_t t[kILP];
 #pragma unroll
-    for (int e = 0; e < kSortILP; ++e) {
+    for (int e = 0; e < kILP; ++e) {
       const int j = jb + e * blockDim.x;
       x[e] = j < te.m ? te.x[j] : -1;
       y[e] = j < te.m ? te.y[j] : 0;
       t[e] = j < te.m ? te.t[j] : 0u;
     }
 #pragma unroll
-    for (int e = 0; e < kSortILP; ++e) {
+    for (int e = 0; e < kILP; ++e) {
       const int j = jb + e * blockDim.x;
       if (j >= te.m) continue;
       uint32_t trel;
