@@ -201,19 +201,30 @@ def _oracle_single_thread(oracle, sl, D, T, X, Y, w, K):
         oracle.set_num_threads(cores)
 
 
-def _kernel_traffic(name: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (source hash recorded beside it)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(path):
-        return None
+# The sources a stage's DRAM traffic depends on: the translation unit of its
+# kernels, plus the pipeline that launches them and the headers they share.
+_COMMON_SRC = ("veckm.cu", "ctx.h", "veckm_internal.h", "chain.cuh", "check.cuh", "phase.cuh")
+_STAGE_SRC = {"gather": "mlp_tc.cu", "sort": "kernels.cu", "pixsum": "kernels.cu",
+              "pool_rows": "kernels.cu", "pool_cols": "kernels.cu", "counts": "kernels.cu"}
+
+
+def stage_digest(name: str) -> str:
+    """Hash of the sources the stage's kernels are built and launched from."""
     src = os.path.join(ROOT, "paper_2504_19417_gb300", "csrc")
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".h", ".cuh")):
-            with open(os.path.join(src, fn), "rb") as f:
-                h.update(f.read())
-    digest = h.hexdigest()[:16]
+    for fn in sorted((_STAGE_SRC[name],) + _COMMON_SRC):
+        with open(os.path.join(src, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _kernel_traffic(name: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the stage's
+    sources are unchanged since the capture (their hash recorded beside it)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path) or name not in _STAGE_SRC:
+        return None
+    digest = stage_digest(name)
     for ln in open(path):
         f = ln.split()
         if len(f) >= 4 and not ln.startswith("#") and f[0] == name and f[1] == workload:
