@@ -66,6 +66,14 @@ def test_layout_edge_cases():
     assert (cw, ch) == (100, 5)
 
 
+@pytest.mark.parametrize("w,h,maxw", [(346, 260, 640), (640, 480, 640), (1, 1, 5), (97, 61, 4096)])
+def test_one_slice_is_its_own_canvas(w, h, maxw):
+    # a batch or plan of one slice runs the pipeline on the slice's own
+    # buffers: that needs the slice at the origin of a canvas of its size
+    ox, oy, cw, ch = vk.canvas_layout([w], [h], 10, 10, maxw)
+    assert (int(ox[0]), int(oy[0]), cw, ch) == (0, 0, w, h)
+
+
 def _slices(seed):
     rng = np.random.default_rng(seed)
     out = []
