@@ -417,10 +417,11 @@ veckm_status veckm_stream_push(veckm_stream *s, const int16_t *d_x, const int16_
   grids_dirty(c);  // the push pools through hbuf into acc
   const uint32_t t_lo = t_hi_us >= (uint64_t)s->window ? t_hi_us - (uint32_t)s->window : 0u;
   const int DV = g.U / 32;
-  // Every kernel of a push after the first is chained to the one before it
-  // (programmatic dependent launch, chain.cuh), except the column pass, which
-  // follows the join with the side stream.  Launch errors are read back below
-  // (cudaPeekAtLastError).
+  // The kernels of a push that follow another of its kernels are chained to
+  // it (programmatic dependent launch, chain.cuh), up to the row pass; the
+  // column pass follows the join with the side stream, and of the kernels
+  // after it only the tensor-core head is chained.  Launch errors are read
+  // back below (cudaPeekAtLastError).
   auto apply = [&](int sign) {
     const dim3 blocks(num_sms() * 8);
     const long long npx = (long long)g.W * g.H;
